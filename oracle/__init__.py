@@ -1,0 +1,157 @@
+"""CPU oracle for the batched GEMM of Eq. (1) (Sec. 2) -- TEST INFRASTRUCTURE ONLY.
+
+C_i = alpha * A_i * B_i + beta * C_i over N independent instances, in FP64
+and complex128, written out as a plain triple loop in C (``oracle_gemm.c``).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The GPU library never calls it and the
+two share no code: the oracle has its own C source, its own build and its own
+loader.
+
+Parity status: pinned. ``tests/test_oracle.py`` checks every entry point
+against brute force on small integer inputs, identity and permutation
+matrices, the Pauli algebra, (AB)^T = B^T A^T, the Kronecker mixed-product
+rule, the BLAS alpha/beta rules and an independent library (numpy.matmul),
+and shows that each of the planted mistakes selectable with ``ORACLE_MUTANT``
+fails at least one of those pins.
+
+Array convention of this wrapper: every operand is a flat 1-D numpy array
+(float64, or complex128 for the complex entry points) holding column-major
+instances; offsets, leading dimensions and strides are in elements.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle_gemm.c")
+_LIB_NAME = "liboracle.so"
+_lock = threading.Lock()
+_libs: dict[str, ctypes.CDLL] = {}
+
+_CFLAGS = ["-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-fopenmp"]
+
+
+def build(out_dir: str | None = None, mutant: int = 0, force: bool = False) -> str:
+    """Compile ``oracle_gemm.c`` with gcc and return the path of the shared library.
+
+    ``mutant`` > 0 builds a variant with one planted mistake (pin tests only).
+    """
+    out_dir = out_dir or _HERE
+    name = _LIB_NAME if mutant == 0 else f"liboracle_mutant{mutant}.so"
+    path = os.path.join(out_dir, name)
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        cmd = ["gcc", *_CFLAGS, f"-DORACLE_MUTANT={int(mutant)}", _SRC, "-o", path + ".tmp"]
+        subprocess.run(cmd, check=True)
+        os.replace(path + ".tmp", path)
+    return path
+
+
+def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
+    i64, dbl, vp = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+    lib.oracle_gemm_r64.argtypes = [i64, i64, i64, dbl, vp, i64, i64, vp, i64, i64, dbl, vp,
+                                    i64, i64, i64]
+    lib.oracle_gemm_c128.argtypes = [i64, i64, i64, vp, vp, i64, i64, vp, i64, i64, vp, vp,
+                                     i64, i64, i64]
+    lib.oracle_gemm_grouped_r64.argtypes = [i64, vp, dbl, vp, vp, dbl, vp]
+    lib.oracle_gemm_grouped_c128.argtypes = [i64, vp, vp, vp, vp, vp, vp]
+    for f in ("oracle_gemm_r64", "oracle_gemm_c128", "oracle_gemm_grouped_r64",
+              "oracle_gemm_grouped_c128"):
+        getattr(lib, f).restype = None
+    lib.oracle_max_threads.restype = ctypes.c_int
+    lib.oracle_set_threads.argtypes = [ctypes.c_int]
+    return lib
+
+
+def load(mutant: int = 0, out_dir: str | None = None) -> ctypes.CDLL:
+    """Load (building first if needed) the oracle library, or a planted-mistake variant."""
+    key = f"{out_dir}:{mutant}"
+    with _lock:
+        if key not in _libs:
+            _libs[key] = _bind(ctypes.CDLL(build(out_dir=out_dir, mutant=mutant)))
+        return _libs[key]
+
+
+def _ptr(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"] or a.ndim == 1
+    return a.ctypes.data
+
+
+def max_threads(lib: ctypes.CDLL | None = None) -> int:
+    return int((lib or load()).oracle_max_threads())
+
+
+def set_threads(t: int, lib: ctypes.CDLL | None = None) -> None:
+    (lib or load()).oracle_set_threads(int(t))
+
+
+def gemm_fixed(m, n, k, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc, strideC,
+               batch, lib: ctypes.CDLL | None = None) -> np.ndarray:
+    """Eq. (1) over a fixed-size batch; updates ``C`` in place and returns it.
+
+    Real when ``C`` is float64, complex when it is complex128 (then alpha and
+    beta are complex scalars).
+    """
+    lib = lib or load()
+    if C.dtype == np.complex128:
+        for x in (A, B):
+            assert x.dtype == np.complex128
+        al = np.array([complex(alpha).real, complex(alpha).imag], dtype=np.float64)
+        be = np.array([complex(beta).real, complex(beta).imag], dtype=np.float64)
+        lib.oracle_gemm_c128(m, n, k, _ptr(al), _ptr(A), lda, strideA, _ptr(B), ldb, strideB,
+                             _ptr(be), _ptr(C), ldc, strideC, batch)
+    else:
+        for x in (A, B, C):
+            assert x.dtype == np.float64
+        lib.oracle_gemm_r64(m, n, k, float(alpha), _ptr(A), lda, strideA, _ptr(B), ldb,
+                            strideB, float(beta), _ptr(C), ldc, strideC, batch)
+    return C
+
+
+def gemm_grouped(table: np.ndarray, alpha, A, B, beta, C,
+                 lib: ctypes.CDLL | None = None) -> np.ndarray:
+    """Eq. (1) over a variable-size batch.
+
+    ``table`` is int64 [count, 9]: m, n, k, lda, ldb, ldc, a_off, b_off, c_off.
+    Updates ``C`` in place and returns it.
+    """
+    lib = lib or load()
+    table = np.ascontiguousarray(table, dtype=np.int64)
+    assert table.ndim == 2 and table.shape[1] == 9
+    count = table.shape[0]
+    if C.dtype == np.complex128:
+        al = np.array([complex(alpha).real, complex(alpha).imag], dtype=np.float64)
+        be = np.array([complex(beta).real, complex(beta).imag], dtype=np.float64)
+        lib.oracle_gemm_grouped_c128(count, _ptr(table), _ptr(al), _ptr(A), _ptr(B), _ptr(be),
+                                     _ptr(C))
+    else:
+        lib.oracle_gemm_grouped_r64(count, _ptr(table), float(alpha), _ptr(A), _ptr(B),
+                                    float(beta), _ptr(C))
+    return C
+
+
+def matmul(A: np.ndarray, B: np.ndarray, lib: ctypes.CDLL | None = None) -> np.ndarray:
+    """Single product A @ B of two 2-D arrays through the oracle (alpha=1, beta=0)."""
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2
+    dt = np.complex128 if (A.dtype == np.complex128 or B.dtype == np.complex128) else np.float64
+    a = np.asfortranarray(A, dtype=dt).ravel(order="F")
+    b = np.asfortranarray(B, dtype=dt).ravel(order="F")
+    c = np.zeros(m * n, dtype=dt)
+    gemm_fixed(m, n, k, 1.0, a, max(m, 1), m * k, b, max(k, 1), k * n, 0.0, c, max(m, 1), m * n,
+               1, lib=lib)
+    return c.reshape((m, n), order="F")
+
+
+def unitarity_drift(C: np.ndarray, lib: ctypes.CDLL | None = None) -> float:
+    """||C^H C - I||_F for one square matrix, the product C^H C taken by the oracle."""
+    n = C.shape[0]
+    G = matmul(np.conj(C.T), C, lib=lib)
+    return float(np.sqrt(np.sum(np.abs(G - np.eye(n)) ** 2)))

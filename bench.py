@@ -1,0 +1,468 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched GEMM hot path (Eq. 1, Sec. 2) on one GB300 per rank.
+
+One step = one grouped call of the library on the whole synthetic batch (one
+persistent launch for FP64; slicer + tensor-core GEMM for split-BF16). The
+default workload is the precision configuration: 20000 square FP64 instances
+with n drawn from {16, 32, 64, 128, 256, 512} (weights .3/.25/.2/.15/.07/.03),
+entries of magnitude 10^U(-4,4) with random signs, alpha = 1, beta = 0.5,
+seed 3. Every mode runs on the same batch: plain FP64 and split-BF16 with 3,
+6 and 9 slices. The headline value is the 9-slice mode (whose error matches
+the FP64 path's), in FP64-equivalent TFLOP/s (2 m n k per instance); the FP64
+mode and the others are reported beside it with their errors against the CPU
+oracle on a sample.
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "batched GEMM TFLOP/s & roofline %: FP64 vs split-BF16 at same error"
+UNIT = "TFLOP/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--config", type=int, choices=[1, 2, 3, 4], default=4)
+    p.add_argument("--count", type=int, default=20000, help="instances (configs 3/4)")
+    p.add_argument("--mode", default="split9", help="headline mode: fp64 or splitS")
+    p.add_argument("--modes", default="fp64,split3,split6,split9")
+    p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def make_batch(config: int, count: int, rank: int):
+    from paper_2203_09353_gb300 import synth
+    if config == 1:
+        return synth.config1(), "config1: 64 real FP64 instances n=32, U[-1,1], seed 0, C=AB"
+    if config == 2:
+        return synth.config2(), ("config2: 4096 complex128 instances n=64, A Hermitian, "
+                                 "B Haar unitary, seed 1, C=AB")
+    if config == 3:
+        seed = 2 + 1000 * rank
+        b = synth.mixed_batch(seed, count, "uniform", 1.0, 0.5, name=f"config3_{count}")
+        return b, (f"config3: {count} real FP64 instances n in {{16..512}} "
+                   f"(w .3/.25/.2/.15/.07/.03), U[-1,1], alpha=1, beta=0.5, seed {seed}")
+    seed = 3 + 1000 * rank
+    b = synth.mixed_batch(seed, count, "loguniform", 1.0, 0.5, name=f"config4_{count}")
+    return b, (f"config4: {count} real FP64 instances n in {{16..512}} "
+               f"(w .3/.25/.2/.15/.07/.03), |x| = 10^U(-4,4) random sign, alpha=1, beta=0.5, "
+               f"seed {seed}")
+
+
+def sample_ids(batch, frac_flops: float) -> np.ndarray:
+    """Every j-th instance (table order is random, so all size classes appear)."""
+    t = batch.table
+    fl = 2.0 * t[:, 0].astype(np.float64) * t[:, 1] * t[:, 2]
+    target = frac_flops * fl.sum()
+    step = max(1, int(round(fl.sum() / max(target, 1.0))))
+    ids = np.arange(0, batch.count, step)
+    return ids
+
+
+def oracle_on(batch, ids):
+    """Runs the CPU oracle on the chosen instances; returns ({id: C}, seconds, flops, threads)."""
+    import oracle
+    from paper_2203_09353_gb300 import synth
+    shapes = [tuple(int(x) for x in batch.table[i, :3]) for i in ids]
+    table, la, lb, lc = synth.pack_table(shapes)
+    A = np.zeros(la, dtype=batch.np_dtype)
+    B = np.zeros(lb, dtype=batch.np_dtype)
+    C = np.zeros(lc, dtype=batch.np_dtype)
+    for j, i in enumerate(ids):
+        m, n, k = shapes[j]
+        A[table[j, 6]:table[j, 6] + m * k] = np.ravel(batch.instance(i, "A"), order="F")
+        B[table[j, 7]:table[j, 7] + k * n] = np.ravel(batch.instance(i, "B"), order="F")
+        C[table[j, 8]:table[j, 8] + m * n] = np.ravel(batch.instance(i, "C"), order="F")
+    lib = oracle.load()
+    threads = oracle.max_threads(lib)
+    t0 = time.perf_counter()
+    oracle.gemm_grouped(table, batch.alpha, A, B, batch.beta, C, lib=lib)
+    dt = time.perf_counter() - t0
+    out = {}
+    for j, i in enumerate(ids):
+        m, n, k = shapes[j]
+        out[int(i)] = C[table[j, 8]:table[j, 8] + m * n].reshape((n, m)).T.copy()
+    flops = float(np.sum([(8.0 if batch.dtype == "c128" else 2.0) * m * n * k
+                          for (m, n, k) in shapes]))
+    return out, dt, flops, threads
+
+
+def calibrated_sample(batch, seconds: float):
+    """Oracle sample sized to take about `seconds` on this host's cores."""
+    ids = sample_ids(batch, 0.002)
+    _, dt, fl, _ = oracle_on(batch, ids)
+    rate = fl / max(dt, 1e-6)
+    frac = min(1.0, seconds * rate / (2.0 * batch.table[:, 0].astype(np.float64)
+                                       @ (batch.table[:, 1] * batch.table[:, 2].astype(np.float64))
+                                       * (4.0 if batch.dtype == "c128" else 1.0)))
+    return sample_ids(batch, max(frac, 0.0005))
+
+
+def sample_errors(batch, C_host: np.ndarray, ref: dict) -> float:
+    worst = 0.0
+    for i, cr in ref.items():
+        m, n, k, lda, ldb, ldc, ao, bo, co = (int(x) for x in batch.table[i])
+        ct = C_host[co:co + ldc * n].reshape((n, ldc)).T[:m, :]
+        den = np.linalg.norm(batch.instance(i, "A")) * np.linalg.norm(batch.instance(i, "B"))
+        e = np.linalg.norm(ct - cr) / den if den > 0 else np.linalg.norm(ct - cr)
+        worst = max(worst, float(e))
+    return worst
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = ["-i", f"GPU-{uuid}" if not uuid.startswith("GPU-") else uuid]
+        except Exception:
+            sel = []
+        self.sel = sel
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", *self.sel, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = np.array([num(r[0]) for r in rows])
+        mx = np.nanmax([num(r[1]) for r in rows])
+        power = np.array([num(r[2]) for r in rows])
+        loaded = sm[power >= np.nanmedian(power)] if len(sm) > 2 else sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4)
+                          if r[4 + j].lower().startswith("active")})
+        return {"sm_mhz": float(np.nanmedian(loaded)), "sm_max_mhz": float(mx),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": float(np.nanmax(power))}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v: float) -> float:
+    if pg is None:
+        return v
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, world, rank, pg):
+    """--impl reference: the CPU oracle, as it stands, on bounded samples of the workload."""
+    if rank != 0:
+        return
+    batch, desc = make_batch(args.config, args.count, 0)
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    ids = calibrated_sample(batch, budget)
+    times, flops, threads = [], 0.0, 1
+    for it in range(args.warmup + args.steps):
+        _, dt, fl, threads = oracle_on(batch, ids)
+        if it >= args.warmup:
+            times.append(dt)
+            flops = fl
+    mean = float(np.mean(times))
+    value = flops / mean / 1e12
+    sample = (f"{len(ids)} of {batch.count} instances (every "
+              f"{max(1, batch.count // max(1, len(ids)))}-th, all size classes), "
+              f"{flops / 1e9:.2f} GFLOP per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "mode": "cpu oracle (plain triple loop, FP64)",
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank, pg)
+        return
+    import torch
+    from paper_2203_09353_gb300 import build as libbuild
+    libbuild.build()
+    import paper_2203_09353_gb300 as bg
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    pk, pk_src = peaks()
+    batch, desc = make_batch(args.config, args.count, rank)
+    flops = batch.flops()
+    A = torch.from_numpy(batch.A).to(dev)
+    B = torch.from_numpy(batch.B).to(dev)
+    C0 = torch.from_numpy(batch.C).to(dev)
+    dtab = torch.from_numpy(batch.table).to(dev)
+    modes = [m for m in args.modes.split(",") if m]
+    if args.mode not in modes:
+        modes.append(args.mode)
+
+    fp64_peak = bg.probe_fp64_peak()
+    cache = os.path.join(tempfile.gettempdir(), "bgemm_autotune.json")
+    plans = {}
+    for m in modes:
+        if m == "fp64":
+            prec, flags = None, bg.BG_PLAN_AUTOTUNE | bg.BG_PLAN_USE_CACHE | bg.BG_PLAN_PROFILE
+        else:
+            prec, flags = bg.precision("split", int(m[5:])), bg.BG_PLAN_PROFILE
+        plans[m] = bg.batched_gemm_plan(batch.dtype, batch.table, prec, flags, cache)
+
+    # --- correctness of every mode: oracle on a sample (rank 0), FP64 path on all instances
+    ref, cpu = None, None
+    if rank == 0 and not args.no_cpu:
+        ids = calibrated_sample(batch, args.cpu_seconds)
+        ref, dt, fl, threads = oracle_on(batch, ids)
+        cpu = {"value": fl / dt / 1e12, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": (f"{len(ids)} of {batch.count} instances (every "
+                          f"{max(1, batch.count // max(1, len(ids)))}-th, all size classes), "
+                          f"{fl / 1e9:.2f} GFLOP in {dt:.2f} s")}
+    outs = {}
+    for m in modes:
+        Cm = C0.clone()
+        bg.batched_gemm_grouped(plans[m], A, B, Cm, batch.alpha, batch.beta)
+        outs[m] = Cm
+    torch.cuda.synchronize()
+    bg.check_device_errors()
+    errs = {}
+    errbuf = torch.zeros(batch.count, dtype=torch.float64, device=dev)
+    for m in modes:
+        e = {}
+        if ref is not None:
+            e["max_vs_oracle_sample"] = sample_errors(batch, outs[m].cpu().numpy(), ref)
+        if "fp64" in outs and m != "fp64":
+            bg.rel_err(batch.dtype, dtab, A, B, outs[m], outs["fp64"], errbuf, batch.count)
+            e["max_vs_fp64_path_all"] = float(errbuf.max().item())
+        errs[m] = e
+    del outs
+
+    # --- timing per mode
+    res = {}
+    clocks = None
+    launches = 0
+    for m in modes:
+        steps = args.fp64_steps if m == "fp64" and m != args.mode else args.steps
+        Cm = C0.clone()
+        for _ in range(args.warmup):
+            bg.batched_gemm_grouped(plans[m], A, B, Cm, batch.alpha, batch.beta)
+        plans[m].kernel_times(reset=True)
+        torch.cuda.synchronize()
+        barrier(pg)
+        headline = m == args.mode
+        if headline:
+            sampler = Clocks(local)
+            sampler.start()
+            bg.launch_count(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            bg.batched_gemm_grouped(plans[m], A, B, Cm, batch.alpha, batch.beta)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(pg)
+        if headline:
+            launches = bg.launch_count()
+            clocks = sampler.stop()
+        ms = e0.elapsed_time(e1) / steps
+        ms = max_over_ranks(pg, ms)
+        kt, calls = plans[m].kernel_times(reset=True)
+        res[m] = {"ms_per_step": ms, "steps": steps,
+                  "value": flops * world / (ms * 1e-3) / 1e12,
+                  "kernel_ms": [kt[0] / max(calls, 1), kt[1] / max(calls, 1)]}
+        del Cm
+
+    # --- roofline of the dominant kernel of each mode
+    t = batch.table.astype(np.float64)
+    esz = 16.0 if batch.dtype == "c128" else 8.0
+    ab_elems = float(np.sum(t[:, 0] * t[:, 2] + t[:, 2] * t[:, 1]))
+    for m in modes:
+        r = res[m]
+        if m == "fp64":
+            k_ms = r["kernel_ms"][0]
+            ach = flops / (k_ms * 1e-3) / 1e12
+            r["roofline"] = {"kernel": "fp64_persistent", "bound": "alu", "achieved": ach,
+                             "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                             "traffic": None,
+                             "peak_source": "DFMA probe measured live (bg_probe_fp64_peak)"}
+        else:
+            s = int(m[5:])
+            pairs = s * (s + 1) // 2
+            k_ms = r["kernel_ms"][1]
+            tf = pairs * flops
+            ach = tf / (k_ms * 1e-3) / 1e12
+            pk_bf16 = pk["bf16_tflops"]
+            r["roofline"] = {"kernel": "split_gemm_kernel (tcgen05)", "bound": "tensor",
+                             "achieved": ach, "peak": pk_bf16, "unit": "TFLOP/s",
+                             "frac": ach / pk_bf16, "traffic": None,
+                             "peak_source": f"bf16 burst, {pk_src} (MEASURED_PEAKS.json)"}
+            sl_ms = r["kernel_ms"][0]
+            sl_bytes = ab_elems * (esz + 2.0 * s * (4.0 if batch.dtype == "c128" else 1.0))
+            r["slicer"] = {"kernel": "split_slice_kernel", "bound": "hbm",
+                           "achieved": sl_bytes / (sl_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+                           "unit": "GB/s",
+                           "frac": sl_bytes / (sl_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                           "ms": sl_ms}
+            r["tensor_tflops_per_step"] = tf / (r["ms_per_step"] * 1e-3) / 1e12
+        r["error"] = errs.get(m, {})
+
+    # --- end to end through the public API with host buffers
+    e2e = None
+    head = args.mode
+    if not args.no_e2e:
+        Ah = torch.from_numpy(batch.A).pin_memory()
+        Bh = torch.from_numpy(batch.B).pin_memory()
+        Ch = torch.from_numpy(batch.C).pin_memory()
+        Co = torch.empty_like(Ch).pin_memory()
+        Cd = torch.empty_like(C0)
+        plan = plans[head]
+
+        def e2e_step():
+            A.copy_(Ah, non_blocking=True)
+            B.copy_(Bh, non_blocking=True)
+            Cd.copy_(Ch, non_blocking=True)
+            bg.batched_gemm_grouped(plan, A, B, Cd, batch.alpha, batch.beta)
+            Co.copy_(Cd, non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(pg)
+        n2 = max(2, args.steps // 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n2):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(pg, e0.elapsed_time(e1) / n2)
+        e2e = {"value": flops * world / (ms * 1e-3) / 1e12, "unit": UNIT,
+               "h2d_bytes_per_step": int(Ah.nbytes + Bh.nbytes + Ch.nbytes),
+               "d2h_bytes_per_step": int(Co.nbytes), "ms_per_step": ms}
+        plan.kernel_times(reset=True)
+
+    if rank != 0:
+        return
+    h = res[head]
+    roof = dict(h["roofline"])
+    line = {
+        "metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world,
+        "steps": h["steps"], "warmup": args.warmup, "ms_per_step": h["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head == "fp64" else "bf16 digit planes, fp32 exact sums, int64/f64 "
+                                              "recombination",
+        "data": "synthetic",
+        "config": {"workload": desc, "mode": head, "count": batch.count,
+                   "gflop_per_step_fp64_equiv": flops / 1e9,
+                   "l2": "inputs (A, B, C) larger than L2, no flush",
+                   "parallelism": f"{world} independent shard(s), no collective"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "modes": res,
+        "fp64_peak_tflops_measured": fp64_peak,
+        "peaks_source": pk_src,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

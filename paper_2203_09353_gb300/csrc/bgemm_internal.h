@@ -1,0 +1,105 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here is part of the public ABI (include/bgemm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bgemm.h"
+
+namespace bg {
+
+// ---- work description --------------------------------------------------------
+
+// Tile programs of the FP64 path. A work item names one program and the part
+// of the batch it covers.
+enum Prog : int16_t {
+  PROG_R64_SMALL = 0,   // one warp per instance, up to 8 instances per CTA
+  PROG_R64_TILE = 1,    // 64x64 output tile, DFMA, 4x4 outputs per thread
+  PROG_R64_DMMA = 2,    // 64x64 output tile, FP64 tensor-core mma.sync m8n8k4
+  PROG_C128_SMALL = 3,  // one warp per complex instance
+  PROG_C128_TILE = 4,   // 32x32 complex output tile, DFMA, 2x2 per thread
+  PROG_COUNT = 5
+};
+
+// One unit of work of the persistent FP64 kernel (16 bytes).
+//  - tile programs: `inst` = instance id, (r0, c0) = first row/col of the tile
+//  - small programs: `inst` = first position in the class-ordered instance
+//    list, `count` = number of consecutive instances (<= 8), r0 = c0 = 0
+struct WorkItem {
+  int32_t inst;
+  int16_t prog;
+  int16_t count;
+  int32_t r0;
+  int32_t c0;
+};
+static_assert(sizeof(WorkItem) == 16, "WorkItem must stay 16 bytes");
+
+constexpr int kSmallPerCta = 8;   // warps (instances) per CTA in the small programs
+constexpr int kFp64Threads = 256;
+
+struct Scalars {
+  double alpha_re, alpha_im, beta_re, beta_im;
+  int alpha_zero, beta_zero;
+};
+
+// Program picked for a size (FP64 path) when no tuned choice exists.
+int default_prog(bg_dtype dt, int64_t m, int64_t n, int64_t k);
+// Output-tile extent of a tile program (rows, cols); small programs return 0.
+void prog_tile(int prog, int* tm, int* tn);
+bool prog_is_small(int prog);
+bool prog_fits(int prog, bg_dtype dt, int64_t m, int64_t n);
+
+// ---- FP64 launchers (fp64.cu) ---------------------------------------------------
+
+cudaError_t launch_fp64_fixed(bg_dtype dt, int prog, int64_t m, int64_t n, int64_t k,
+                              const Scalars& s, const void* A, int64_t lda, int64_t sA,
+                              const void* B, int64_t ldb, int64_t sB, void* C, int64_t ldc,
+                              int64_t sC, int64_t batch, int grid_cap, cudaStream_t st);
+
+cudaError_t launch_fp64_table(bg_dtype dt, const int64_t* d_table, const int32_t* d_order,
+                              const WorkItem* d_items, int64_t n_items, const void* A,
+                              const void* B, void* C, const Scalars& s, int grid,
+                              cudaStream_t st);
+
+cudaError_t launch_fp64_chain(bg_dtype dt, const int64_t* d_wn, const int64_t* d_woff,
+                              const int64_t* d_pool_off, const int64_t* d_pool_n,
+                              int32_t pool_count, const int32_t* d_order,
+                              const int32_t* d_idx_row, const WorkItem* d_items, int64_t n_items,
+                              const void* U, const void* Cin, void* Cout, int grid,
+                              cudaStream_t st);
+
+// Resident CTAs per SM of the persistent FP64 kernel (for grid sizing).
+int fp64_blocks_per_sm(bg_dtype dt);
+
+// ---- split-BF16 path (split.cu) ---------------------------------------------------
+
+struct SplitParams;  // defined in split.cu
+
+// ---- measurement and diagnostics (util.cu) ------------------------------------------
+
+cudaError_t launch_rel_err(bg_dtype dt, int64_t count, const int64_t* d_table, const void* A,
+                           const void* B, const void* Ct, const void* Cr, double* out,
+                           cudaStream_t st);
+cudaError_t launch_drift(bg_dtype dt, int64_t count, const int64_t* d_n, const int64_t* d_off,
+                         const void* C, double* out, cudaStream_t st);
+cudaError_t launch_bounded_wait(int64_t spin_limit, int* d_err, cudaStream_t st);
+cudaError_t run_fp64_peak_probe(int mma_kind, int sms, double* tflops, cudaStream_t st);
+
+// Device error word layout: [0] = first error code, [1] = location id,
+// [2] = detail, [3] = count of events.
+enum DevErrLoc : int {
+  ERRLOC_NONE = 0,
+  ERRLOC_TEST_WAIT = 1,
+  ERRLOC_SPLIT_FULL_BARRIER = 2,
+  ERRLOC_SPLIT_EMPTY_BARRIER = 3,
+  ERRLOC_SPLIT_ACC_FULL = 4,
+  ERRLOC_SPLIT_ACC_EMPTY = 5,
+  ERRLOC_SPLIT_TMEM_ALLOC = 6,
+  ERRLOC_CHAIN_INDEX = 7
+};
+
+// Host bookkeeping.
+void count_launch(int n = 1);
+
+}  // namespace bg

@@ -1,0 +1,1537 @@
+// Split-precision path of Eq. (1): FP64 operands cut into BF16 digit planes,
+// multiplied on the 5th-generation tensor cores (tcgen05, accumulators in
+// TMEM) with FP32 sums that are exact by construction, recombined exactly
+// in integer arithmetic and rounded once to FP64.
+//
+// The paper computes its GEMMs in complex FP64 through cuBLAS (Sec. 4) and has
+// no such mode; it is the GB300 answer to an FP64 pipe that issues only 2
+// DFMA per clock per SM. The method, step by step:
+//
+//  1. Scale. Row i of A gets the exponent e_i with max_p |A_ip| < 2^e_i, column
+//     j of B the exponent f_j with max_p |B_pj| < 2^f_j (0 for an all-zero line).
+//  2. Cut. a = A_ip 2^(beta - e_i) lies in (-2^beta, 2^beta). Its fixed-point
+//     value N = round(a 2^(beta (s-1))) is written in balanced base 2^beta:
+//     N = sum_{p=1..s} d_p 2^(beta (s-p)), |d_1| <= 2^beta, |d_p| <= 2^(beta-1)
+//     (p >= 2). Every digit is an integer of at most 9 significant bits, hence
+//     exact in BF16. Same for B per column.
+//  3. Multiply. For each level t = p + q (2 <= t <= s+1, the triangular set of
+//     plane pairs), L_t = sum_{p+q=t} D_p^A D_q^B on the tensor cores. K is cut
+//     into chunks small enough that every partial sum stays below 2^24, so the
+//     FP32 accumulation is exact; the chunk size per level follows from the
+//     digit bounds (host: level_chunks()).
+//  4. Recombine. G_ij = sum_t L_t 2^(-beta (t-2)) is accumulated per element in
+//     a 64-bit fixed-point integer whose frame is set from bounds on the row and
+//     column digit norms (so it cannot overflow and keeps >= 60 bits of the
+//     result), then converted to FP64 with one correct rounding and scaled by
+//     2^(e_i + f_j - 2 beta). alpha and beta of Eq. (1) are applied in FP64.
+//
+// Complex instances run as real ones through the real representation of a
+// complex number: B and C viewed as real matrices with interleaved (re, im)
+// rows (k' = 2k, ldb' = 2 ldb; m' = 2m, ldc' = 2 ldc) and each entry a of A
+// expanded to [[re a, -im a], [im a, re a]]; exponents are then shared by the
+// real and imaginary parts of a row of A / a column of B.
+//
+// Kernels:
+//  * split_slice_kernel: one CTA per 128-line block of A (rows) or B (columns):
+//    exponents, digit planes written as pre-swizzled 128 x 64 BF16 tiles
+//    (the exact SWIZZLE_128B K-major shared-memory image), per-line norm
+//    exponents. Integer arithmetic only.
+//  * split_gemm_kernel: persistent, one CTA per SM, warp-specialised: warp 0
+//    streams tile pairs with 1-D TMA bulk copies (cp.async.bulk) into a
+//    6-stage mbarrier ring, warp 1 issues tcgen05.mma (M=128, N=128, K=16)
+//    into two TMEM accumulator slots, warps 2-9 drain the slots with
+//    tcgen05.ld and do the integer recombination and the FP64 epilogue.
+//    Small instances are packed along the diagonal of a 128 x 128 unit.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "split.h"
+
+namespace bg {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int kTileBytes = BM * BK * 2;  // 16 KiB, also BN x BK for B
+constexpr int kStages = 6;
+constexpr int kGemmThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr int kMetaStride = 264;  // int32 per block: e[128], R[128], max R at [256]
+constexpr int kTmemCols = 256;    // two accumulator slots of BN columns
+constexpr int kSliceThreads = 256;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any single wait
+
+struct SInst {
+  int64_t a_off, b_off, c_off;  // user element offsets
+  int64_t lda, ldb, ldc;        // user elements
+  int32_t m, n, k;              // user sizes
+  int32_t pad;
+};
+
+struct SliceJob {
+  int64_t tile0;  // first tile (plane 1, k-block 0) of the block
+  int32_t blk;    // block id = meta index
+  int32_t pos;    // first position in the order list
+  int16_t side;   // 0: A block (rows), 1: B block (columns)
+  int16_t g;      // instances stacked in the block
+  int16_t span;   // lines per stacked instance (virtual rows of A / columns of B)
+  int16_t nkb;    // k-blocks of 64
+  int32_t org;    // first line of the block within its instance (big instances)
+  int32_t kv;     // virtual k' of the instances
+};
+
+struct SplitUnit {
+  int64_t a_tile0, b_tile0;  // first tiles (chain mode: a_tile0 = row-block offset in tiles)
+  int32_t a_blk, b_blk;      // meta blocks (chain mode: a_blk = row block index)
+  int32_t pos;               // order position of the (first) instance
+  int16_t g;                 // packed instances (1 = a tile of one instance)
+  int16_t nkb;               // k-blocks
+  int16_t kmma_last;         // MMAs (K = 16) in the last k-block
+  int16_t mrow;              // virtual rows per packed instance
+  int16_t ncol;              // columns per packed instance
+  int16_t pad;
+  int32_t r0, c0;            // tile origin in the instance (virtual rows, columns)
+};
+
+struct LevelTable {
+  int8_t kcb[kMaxSlices + 3];  // chunk size in k-blocks for level t (index t)
+};
+
+struct SliceArgs {
+  const SliceJob* jobs;
+  int64_t njobs;
+  const SInst* instA;
+  const SInst* instB;
+  const int32_t* orderA;
+  const int32_t* orderB;
+  const double* A;
+  const double* B;
+  uint8_t* tilesA;
+  uint8_t* tilesB;
+  int32_t* metaA;
+  int32_t* metaB;
+  int cplx, s, beta;
+};
+
+struct GemmArgs {
+  const SplitUnit* units;
+  int64_t nunits;
+  const SInst* inst;
+  const int32_t* order;
+  const uint8_t* tilesA;
+  const uint8_t* tilesB;
+  const int32_t* metaA;
+  const int32_t* metaB;
+  double* C;
+  const int32_t* idx;         // chain mode: pool index per walker, else nullptr
+  const int64_t* pool_tile0;  // chain mode: first tile of each pool entry
+  const int32_t* pool_blk0;   // chain mode: first meta block of each pool entry
+  const SInst* pool;          // chain mode: pool entries (sizes)
+  int32_t pool_count;         // chain mode: number of pool entries
+  Scalars sc;
+  int cplx, s, beta, skip_product;
+  LevelTable lv;
+  int* err;
+};
+
+// ---- small device helpers --------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void record_error(int* err, int code, int loc, int detail) {
+  if (atomicCAS(err, 0, code) == 0) {
+    err[1] = loc;
+    err[2] = detail;
+  }
+  atomicAdd(err + 3, 1);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the phase with the given parity; gives up (returns false) after
+// kWaitNs or when another role has raised the abort flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          const volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long deadline = globaltimer_ns() + kWaitNs;
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (globaltimer_ns() > deadline) return false;
+  }
+  return true;
+}
+
+// Waits for the phase with the given parity for at most kWaitNs, ignoring the
+// abort flag (used to let in-flight copies and MMAs finish before exit).
+__device__ __forceinline__ bool mbar_wait_time(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long deadline = globaltimer_ns() + kWaitNs;
+  while (!mbar_try_wait(bar, parity))
+    if (globaltimer_ns() > deadline) return false;
+  return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (the layout the slicer writes).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = BF16, D = FP32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---- digits --------------------------------------------------------------------------------
+
+// Exponent e with |x| < 2^e for the largest magnitude of a line, from the bit
+// pattern of that magnitude (0 for an all-zero line).
+__device__ __forceinline__ int line_exponent(unsigned long long maxbits) {
+  if (maxbits == 0) return 0;
+  const int eb = (int)(maxbits >> 52) & 0x7FF;
+  if (eb != 0) return eb - 1022;
+  const unsigned long long frac = maxbits & ((1ull << 52) - 1);
+  return (64 - __clzll((long long)frac)) - 1074;
+}
+
+// Per-kernel constants of the digit cut: digit width beta, half = 2^(beta-1),
+// the balancing bias sum_{p=1..S} half 2^(beta (S-p)) and 2^-beta.
+struct DigitCtx {
+  int beta, half, mask;
+  __int128 bias;
+  float step;
+};
+
+template <int S>
+__device__ __forceinline__ DigitCtx digit_ctx(int beta) {
+  DigitCtx c;
+  c.beta = beta;
+  c.half = 1 << (beta - 1);
+  c.mask = (1 << beta) - 1;
+  c.bias = 0;
+#pragma unroll
+  for (int p = 0; p < S; ++p) c.bias = (c.bias << beta) + c.half;
+  c.step = __int_as_float((127 - beta) << 23);
+  return c;
+}
+
+// Balanced base-2^beta digits of round(x 2^(S beta - e)), most significant
+// first: d[0] = d_1 ... d[S-1] = d_S, with |d_1| <= 2^beta and
+// -2^(beta-1) <= d_p < 2^(beta-1) for p >= 2. The magnitude is rounded half
+// up, then the sign applied; the balanced form comes from adding the bias
+// and reading beta-bit fields. Returns the absolute digit weight
+// alpha = sum_p |d_p| 2^(-beta (p-1)) (FP32) used for the norm bound.
+template <int S>
+__device__ __forceinline__ float make_digits(double x, int e, const DigitCtx& c, int* d) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int eb = (int)(bits >> 52) & 0x7FF;
+  unsigned long long M = bits & ((1ull << 52) - 1);
+  int q;
+  if (eb == 0) {
+    q = -1074;
+  } else {
+    M |= 1ull << 52;
+    q = eb - 1075;
+  }
+  const int sh = q - e + S * c.beta;
+  unsigned __int128 N = 0;
+  if (M != 0) {
+    if (sh >= 0) {
+      N = (unsigned __int128)M << sh;
+    } else if (sh > -64) {
+      N = (unsigned __int128)((M + (1ull << (-sh - 1))) >> (-sh));
+    }
+  }
+  __int128 Np = ((bits >> 63) ? -(__int128)N : (__int128)N) + c.bias;
+#pragma unroll
+  for (int p = S - 1; p >= 1; --p) {
+    d[p] = (int)((long long)Np & c.mask) - c.half;
+    Np >>= c.beta;
+  }
+  d[0] = (int)(long long)Np - c.half;
+  float alpha = 0.f, w = 1.f;
+#pragma unroll
+  for (int p = 0; p < S; ++p) {
+    alpha = fmaf((float)abs(d[p]), w, alpha);
+    w *= c.step;
+  }
+  return alpha;
+}
+
+// BF16 bit pattern of a small integer (|d| <= 256), exact.
+__device__ __forceinline__ uint32_t bf16_of_int(int d) {
+  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+  return __float_as_uint(f) >> 16;
+}
+
+// Norm exponent: smallest R with sqrt(S) < 2^R (with a margin for the FP32
+// rounding of S); -126 for S == 0.
+__device__ __forceinline__ int norm_exponent(float S) {
+  if (!(S > 0.f)) return -126;
+  const float S2 = S * 1.03125f;
+  const int E = (int)((__float_as_uint(S2) >> 23) & 0xFF) - 126;
+  return (E + 1) >> 1;
+}
+
+// Value of the virtual real matrix A' (m' x k') at (r, q); A is real or
+// complex (expanded 2x2 per entry).
+__device__ __forceinline__ double valA(const double* A, const SInst& in, int cplx, int r, int q) {
+  if (!cplx) return __ldg(A + in.a_off + r + (int64_t)q * in.lda);
+  const double2 z =
+      __ldg(reinterpret_cast<const double2*>(A) + in.a_off + (r >> 1) + (int64_t)(q >> 1) * in.lda);
+  const int sel = ((r & 1) << 1) | (q & 1);
+  return sel == 0 ? z.x : sel == 1 ? -z.y : sel == 2 ? z.y : z.x;
+}
+
+// Value of B' (k' x n) at (q, c): the real view of B.
+__device__ __forceinline__ double valB(const double* B, const SInst& in, int cplx, int q, int c) {
+  if (!cplx) return __ldg(B + in.b_off + q + (int64_t)c * in.ldb);
+  return __ldg(B + 2 * in.b_off + q + (int64_t)c * 2 * in.ldb);
+}
+
+// ---- slicer ----------------------------------------------------------------------------------
+
+template <int S>
+__global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceArgs a) {
+  const DigitCtx dc = digit_ctx<S>(a.beta);
+  __shared__ unsigned long long s_max[2][128];
+  __shared__ float s_n2[2][128];
+  __shared__ int s_e[128];
+  __shared__ int s_R[128];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int64_t jb = blockIdx.x; jb < a.njobs; jb += gridDim.x) {
+    const SliceJob J = a.jobs[jb];
+    const bool isA = J.side == 0;
+    const int kv = J.kv;
+    // ---- phase 1: line maxima
+    if (isA) {
+      const int l = t & 127, h = t >> 7;
+      const int li = l / J.span;
+      unsigned long long mx = 0;
+      if (li < J.g) {
+        const SInst in = a.instA[a.orderA[J.pos + li]];
+        const int r = J.org + l % J.span;
+        const int mv = a.cplx ? 2 * in.m : in.m;
+        if (r < mv)
+          for (int q = h; q < kv; q += 2) {
+            const unsigned long long b =
+                (unsigned long long)__double_as_longlong(valA(a.A, in, a.cplx, r, q)) &
+                0x7FFFFFFFFFFFFFFFull;
+            mx = b > mx ? b : mx;
+          }
+      }
+      s_max[h][l] = mx;
+    } else {
+      for (int l = warp * 16; l < warp * 16 + 16; ++l) {
+        const int li = l / J.span;
+        unsigned long long mx = 0;
+        if (li < J.g) {
+          const SInst in = a.instB[a.orderB[J.pos + li]];
+          const int c = J.org + l % J.span;
+          if (c < in.n)
+            for (int q = lane; q < kv; q += 32) {
+              const unsigned long long b =
+                  (unsigned long long)__double_as_longlong(valB(a.B, in, a.cplx, q, c)) &
+                  0x7FFFFFFFFFFFFFFFull;
+              mx = b > mx ? b : mx;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+          mx = y > mx ? y : mx;
+        }
+        if (lane == 0) {
+          s_max[0][l] = mx;
+          s_max[1][l] = 0;
+        }
+      }
+    }
+    __syncthreads();
+    if (t < 128) {
+      const unsigned long long m0 = s_max[0][t], m1 = s_max[1][t];
+      s_e[t] = line_exponent(m0 > m1 ? m0 : m1);
+    }
+    __syncthreads();
+    // ---- phase 2: digit planes
+    int d[S];
+    if (isA) {
+      const int l = t & 127, h = t >> 7;
+      const int li = l / J.span;
+      const bool lvalid = li < J.g;
+      SInst in{};
+      int r = 0, mv = 0;
+      if (lvalid) {
+        in = a.instA[a.orderA[J.pos + li]];
+        r = J.org + l % J.span;
+        mv = a.cplx ? 2 * in.m : in.m;
+      }
+      const bool rvalid = lvalid && r < mv;
+      const int e = s_e[l];
+      float n2 = 0.f;
+      for (int kb = 0; kb < J.nkb; ++kb) {
+        for (int i = 0; i < 4; ++i) {
+          const int cc = h + 2 * i;
+          uint32_t w[S][4];
+#pragma unroll
+          for (int u = 0; u < 8; u += 2) {
+            const int q0 = kb * BK + 8 * cc + u;
+            const double x0 = (rvalid && q0 < kv) ? valA(a.A, in, a.cplx, r, q0) : 0.0;
+            const double x1 = (rvalid && q0 + 1 < kv) ? valA(a.A, in, a.cplx, r, q0 + 1) : 0.0;
+            int d1[S];
+            const float al0 = make_digits<S>(x0, e, dc, d);
+            const float al1 = make_digits<S>(x1, e, dc, d1);
+            n2 = fmaf(al0, al0, n2);
+            n2 = fmaf(al1, al1, n2);
+            #pragma unroll
+            for (int p = 0; p < S; ++p) w[p][u >> 1] = bf16_of_int(d[p]) | (bf16_of_int(d1[p]) << 16);
+          }
+          const int64_t rowoff = (int64_t)l * 128 + ((cc ^ (l & 7)) << 4);
+#pragma unroll
+          for (int p = 0; p < S; ++p) {
+            uint8_t* dst = a.tilesA + (J.tile0 + (int64_t)p * J.nkb + kb) * kTileBytes + rowoff;
+            *reinterpret_cast<uint4*>(dst) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+          }
+        }
+      }
+      s_n2[h][l] = n2;
+    } else {
+      float n2[4] = {0.f, 0.f, 0.f, 0.f};
+      const int cc = lane & 7;
+      for (int kb = 0; kb < J.nkb; ++kb) {
+        for (int it = 0; it < 4; ++it) {
+          const int l = it * 32 + warp * 4 + (lane >> 3);
+          const int li = l / J.span;
+          bool cvalid = false;
+          SInst in{};
+          int c = 0;
+          if (li < J.g) {
+            in = a.instB[a.orderB[J.pos + li]];
+            c = J.org + l % J.span;
+            cvalid = c < in.n;
+          }
+          const int e = s_e[l];
+          uint32_t w[S][4];
+#pragma unroll
+          for (int u = 0; u < 8; u += 2) {
+            const int q0 = kb * BK + 8 * cc + u;
+            const double x0 = (cvalid && q0 < kv) ? valB(a.B, in, a.cplx, q0, c) : 0.0;
+            const double x1 = (cvalid && q0 + 1 < kv) ? valB(a.B, in, a.cplx, q0 + 1, c) : 0.0;
+            int d1[S];
+            const float al0 = make_digits<S>(x0, e, dc, d);
+            const float al1 = make_digits<S>(x1, e, dc, d1);
+            n2[it] = fmaf(al0, al0, n2[it]);
+            n2[it] = fmaf(al1, al1, n2[it]);
+            #pragma unroll
+            for (int p = 0; p < S; ++p) w[p][u >> 1] = bf16_of_int(d[p]) | (bf16_of_int(d1[p]) << 16);
+          }
+          const int64_t rowoff = (int64_t)l * 128 + ((cc ^ (l & 7)) << 4);
+#pragma unroll
+          for (int p = 0; p < S; ++p) {
+            uint8_t* dst = a.tilesB + (J.tile0 + (int64_t)p * J.nkb + kb) * kTileBytes + rowoff;
+            *reinterpret_cast<uint4*>(dst) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+          }
+        }
+      }
+      for (int it = 0; it < 4; ++it) {
+        float v = n2[it];
+        v += __shfl_xor_sync(0xFFFFFFFFu, v, 1);
+        v += __shfl_xor_sync(0xFFFFFFFFu, v, 2);
+        v += __shfl_xor_sync(0xFFFFFFFFu, v, 4);
+        const int l = it * 32 + warp * 4 + (lane >> 3);
+        if (cc == 0) {
+          s_n2[0][l] = v;
+          s_n2[1][l] = 0.f;
+        }
+      }
+    }
+    __syncthreads();
+    // ---- phase 3: meta (exponent, norm exponent, block max of the norm exponent)
+    int32_t* meta = (isA ? a.metaA : a.metaB) + (int64_t)J.blk * kMetaStride;
+    if (t < 128) {
+      const int R = norm_exponent(s_n2[0][t] + s_n2[1][t]);
+      s_R[t] = R;
+      meta[t] = s_e[t];
+      meta[128 + t] = R;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int mx = -126;
+      for (int l = lane; l < 128; l += 32) mx = max(mx, s_R[l]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+      if (lane == 0) meta[256] = mx;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- GEMM --------------------------------------------------------------------------------------
+
+struct GemmSmem {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
+  uint64_t mma_done;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+constexpr size_t kGemmSmemBytes = 1024 + 2 * kStages * kTileBytes + sizeof(GemmSmem);
+
+// Resolves the tiles and meta block of a unit. In chain mode the A side is
+// the pool matrix named by the walker's index for this step; an index out of
+// range or naming a matrix of another size makes the unit invalid (returns
+// false): every role then skips it and the walker's output is left as is.
+__device__ __forceinline__ bool unit_tiles(const GemmArgs& g, const SplitUnit& U, int64_t* at,
+                                           int64_t* bt, int* ablk) {
+  *bt = U.b_tile0;
+  if (g.idx) {
+    const int w = g.order[U.pos];
+    const int j = g.idx[w];
+    if (j < 0 || j >= g.pool_count || g.pool[j].n != g.inst[w].n) {
+      *at = 0;
+      *ablk = 0;
+      return false;
+    }
+    *at = g.pool_tile0[j] + U.a_tile0;
+    *ablk = g.pool_blk0[j] + U.a_blk;
+    return true;
+  }
+  *at = U.a_tile0;
+  *ablk = U.a_blk;
+  return true;
+}
+
+__device__ __forceinline__ double fixed_to_double(long long a, int E) {
+  if (a == 0) return 0.0;
+  const unsigned long long sign = a < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long u = a < 0 ? (unsigned long long)(-a) : (unsigned long long)a;
+  const int lz = __clzll((long long)u);
+  const unsigned long long un = u << lz;
+  unsigned long long mant = un >> 11;
+  const unsigned long long rem = un & 0x7FFull;
+  mant += (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
+  int ex = 63 - lz + E;
+  if (mant >> 53) {
+    mant >>= 1;
+    ex += 1;
+  }
+  const int biased = ex + 1023;
+  if (biased >= 1 && biased <= 2046)
+    return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) |
+                                            (mant & ((1ull << 52) - 1))));
+  const double v = scalbn((double)mant, ex - 52);
+  return sign ? -v : v;
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint8_t* stA = smem;
+  uint8_t* stB = smem + kStages * kTileBytes;
+  GemmSmem& S = *reinterpret_cast<GemmSmem*>(smem + 2 * kStages * kTileBytes);
+  volatile int* abort_flag = &S.abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = g.s;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&S.full[i], 1);
+      mbar_init(&S.empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&S.acc_full[i], 1);
+      mbar_init(&S.acc_empty[i], kEpiWarps);
+    }
+    mbar_init(&S.mma_done, 1);
+    S.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&S.tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = S.tmem_base;
+
+  if (warp == 0) {
+    // ---------------- producer: TMA bulk copies of tile pairs ----------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < g.nunits && ok && !g.skip_product; u += gridDim.x) {
+        const SplitUnit U = g.units[u];
+        int64_t at, bt;
+        int ablk;
+        if (!unit_tiles(g, U, &at, &bt, &ablk)) continue;
+        for (int t = 2; t <= s + 1 && ok; ++t) {
+          const int kc = g.lv.kcb[t];
+          for (int kb0 = 0; kb0 < U.nkb && ok; kb0 += kc) {
+            const int kb1 = min((int)U.nkb, kb0 + kc);
+            for (int p = 1; p < t && ok; ++p) {
+              const int q = t - p;
+              for (int kb = kb0; kb < kb1; ++kb) {
+                const int st = it % kStages;
+                const uint32_t use = it / kStages;
+                if (use > 0 && !mbar_wait(&S.empty[st], (use - 1) & 1, abort_flag)) {
+                  record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_EMPTY_BARRIER, (int)u);
+                  *abort_flag = 1;
+                  ok = false;
+                  break;
+                }
+                mbar_arrive_expect_tx(&S.full[st], 2 * kTileBytes);
+                bulk_g2s(stA + st * kTileBytes,
+                         g.tilesA + (at + (int64_t)(p - 1) * U.nkb + kb) * kTileBytes, kTileBytes,
+                         &S.full[st]);
+                bulk_g2s(stB + st * kTileBytes,
+                         g.tilesB + (bt + (int64_t)(q - 1) * U.nkb + kb) * kTileBytes, kTileBytes,
+                         &S.full[st]);
+                ++it;
+              }
+            }
+          }
+        }
+      }
+      // let every copy this thread started land before the CTA can exit
+      const uint32_t first = it > (uint32_t)kStages ? it - kStages : 0;
+      for (uint32_t j = first; j < it; ++j) mbar_wait_time(&S.full[j % kStages], (j / kStages) & 1);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(BM, BN);
+      uint32_t it = 0, drain = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < g.nunits && ok && !g.skip_product; u += gridDim.x) {
+        const SplitUnit U = g.units[u];
+        int64_t at_, bt_;
+        int ablk_;
+        if (!unit_tiles(g, U, &at_, &bt_, &ablk_)) continue;
+        for (int t = 2; t <= s + 1 && ok; ++t) {
+          const int kc = g.lv.kcb[t];
+          for (int kb0 = 0; kb0 < U.nkb && ok; kb0 += kc) {
+            const int kb1 = min((int)U.nkb, kb0 + kc);
+            const int slot = drain & 1;
+            const uint32_t suse = drain >> 1;
+            if (suse > 0 && !mbar_wait(&S.acc_empty[slot], (suse - 1) & 1, abort_flag)) {
+              record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_ACC_EMPTY, (int)u);
+              *abort_flag = 1;
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t d_tmem = tmem_base + slot * BN;
+            uint32_t acc = 0;
+            for (int p = 1; p < t && ok; ++p) {
+              for (int kb = kb0; kb < kb1; ++kb) {
+                const int st = it % kStages;
+                const uint32_t use = it / kStages;
+                if (!mbar_wait(&S.full[st], use & 1, abort_flag)) {
+                  record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_FULL_BARRIER, (int)u);
+                  *abort_flag = 1;
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+                const uint64_t ad = sw128_desc(smem_u32(stA + st * kTileBytes));
+                const uint64_t bd = sw128_desc(smem_u32(stB + st * kTileBytes));
+                const int nmma = (kb == U.nkb - 1) ? U.kmma_last : 4;
+                for (int kk = 0; kk < nmma; ++kk) {
+                  umma_bf16(d_tmem, ad + 2 * kk, bd + 2 * kk, idesc, acc);
+                  acc = 1;
+                }
+                umma_commit(&S.empty[st]);
+                ++it;
+              }
+            }
+            if (!ok) break;
+            umma_commit(&S.acc_full[slot]);
+            ++drain;
+          }
+        }
+      }
+      // all MMAs issued by this thread are complete once mma_done fires
+      umma_commit(&S.mma_done);
+      mbar_wait_time(&S.mma_done, 0);
+    }
+  } else {
+    // ---------------- epilogue: drain, recombine, store ----------------
+    const int ew = warp - 2;
+    const int quad = warp & 3;
+    const int half = ew >> 2;
+    const int row = quad * 32 + lane;
+    const uint32_t tq = tmem_base + ((uint32_t)(quad * 32) << 16) + half * 64;
+    const bool alpha_one = g.sc.alpha_re == 1.0 && g.sc.alpha_im == 0.0;
+    uint32_t drain = 0;
+    bool ok = true;
+    for (int64_t u = blockIdx.x; u < g.nunits && ok; u += gridDim.x) {
+      const SplitUnit U = g.units[u];
+      int64_t at, bt;
+      int ablk;
+      if (!unit_tiles(g, U, &at, &bt, &ablk)) {
+        if (warp == 2 && lane == 0)
+          record_error(g.err, BG_ERR_INVALID_ARG, ERRLOC_CHAIN_INDEX, (int)g.order[U.pos]);
+        continue;
+      }
+      const int32_t* ma = g.metaA + (int64_t)ablk * kMetaStride;
+      const int32_t* mb = g.metaB + (int64_t)U.b_blk * kMetaStride;
+      const int e_i = ma[row];
+      const int F = ma[128 + row] + mb[256] + 1;
+      long long acc[64];
+#pragma unroll
+      for (int j = 0; j < 64; ++j) acc[j] = 0;
+      if (!g.skip_product) {
+        for (int t = 2; t <= s + 1 && ok; ++t) {
+          const int kc = g.lv.kcb[t];
+          int sh = 62 - F - g.beta * (t - 2);
+          sh = max(-63, min(62, sh));
+          const int lsh = sh > 0 ? sh : 0, rsh = sh < 0 ? -sh : 0;
+          const long long rnd = rsh > 0 ? (1ll << (rsh - 1)) : 0ll;
+          for (int kb0 = 0; kb0 < U.nkb && ok; kb0 += kc) {
+            const int slot = drain & 1;
+            const uint32_t suse = drain >> 1;
+            bool got = true;
+            if (lane == 0) got = mbar_wait(&S.acc_full[slot], suse & 1, abort_flag);
+            got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
+            if (!got) {
+              if (lane == 0) {
+                record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_ACC_FULL, (int)u);
+                *abort_flag = 1;
+              }
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int c2 = 0; c2 < 2; ++c2) {
+              uint32_t v[32];
+              tmem_ld32(tq + slot * BN + 32 * c2, v);
+              tmem_ld_wait();
+              if (c2 == 1) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.acc_empty[slot]);
+              }
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const long long L = (long long)__float2int_rn(__uint_as_float(v[j]));
+                acc[32 * c2 + j] += ((L << lsh) + rnd) >> rsh;
+              }
+            }
+            ++drain;
+          }
+        }
+      }
+      if (!ok) break;
+      // ---- final: exact conversion, alpha/beta, store
+      const int g_count = U.g;
+      int li = 0, rr, inst_pos;
+      bool rvalid;
+      if (g_count > 1) {
+        li = row / U.mrow;
+        rr = row - li * U.mrow;
+        rvalid = li < g_count;
+        inst_pos = U.pos + (rvalid ? li : 0);
+      } else {
+        rr = U.r0 + row;
+        inst_pos = U.pos;
+        rvalid = true;
+      }
+      const SInst in = g.inst[g.order[inst_pos]];
+      const int mv = g.cplx ? 2 * in.m : in.m;
+      rvalid = rvalid && rr < mv;
+      const int64_t cbase = (g.cplx ? 2 * in.c_off : in.c_off) + rr;
+      const int64_t ldcv = g.cplx ? 2 * in.ldc : in.ldc;
+      const int Ebase = F - 62 + e_i - 2 * g.beta;
+#pragma unroll
+      for (int j = 0; j < 64; ++j) {
+        const int col = half * 64 + j;
+        int cc;
+        bool valid;
+        if (g_count > 1) {
+          const int lj = col / U.ncol;
+          cc = col - lj * U.ncol;
+          valid = rvalid && lj == li;
+        } else {
+          cc = U.c0 + col;
+          valid = rvalid && cc < in.n;
+        }
+        const int f_j = mb[col];
+        double x = valid ? fixed_to_double(acc[j], Ebase + f_j) : 0.0;
+        double* cp = g.C + cbase + (int64_t)cc * ldcv;
+        if (!g.cplx) {
+          if (valid) {
+            double v = alpha_one ? x : g.sc.alpha_re * x;
+            if (g.skip_product) v = 0.0;
+            if (!g.sc.beta_zero) v = fma(g.sc.beta_re, *cp, v);
+            *cp = v;
+          }
+        } else {
+          const double xp = __shfl_xor_sync(0xFFFFFFFFu, x, 1);
+          const double c = (valid && !g.sc.beta_zero) ? *cp : 0.0;
+          const double cpn = __shfl_xor_sync(0xFFFFFFFFu, c, 1);
+          if (valid) {
+            const double sgn = (rr & 1) ? 1.0 : -1.0;  // im row: +, re row: -
+            double v = g.skip_product ? 0.0
+                                      : fma(g.sc.alpha_re, x, sgn * g.sc.alpha_im * xp);
+            if (!g.sc.beta_zero) v = fma(g.sc.beta_re, c, fma(sgn * g.sc.beta_im, cpn, v));
+            *cp = v;
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kTmemCols));
+  }
+}
+
+// ---- standalone plane cut (exposed for checking the digit arithmetic) ------------------------
+
+__global__ void planes_exp_kernel(int64_t m, int64_t k, const double* X, int64_t ldx, int axis,
+                                  int32_t* exps) {
+  const int64_t lines = axis == 0 ? m : k;
+  const int64_t len = axis == 0 ? k : m;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < lines;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long mx = 0;
+    for (int64_t i = 0; i < len; ++i) {
+      const double x = axis == 0 ? X[l + i * ldx] : X[i + l * ldx];
+      const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+      mx = b > mx ? b : mx;
+    }
+    exps[l] = line_exponent(mx);
+  }
+}
+
+template <int S>
+__global__ void planes_digit_kernel(int64_t m, int64_t k, const double* X, int64_t ldx, int axis,
+                                    int beta, const int32_t* exps, uint16_t* digits) {
+  const DigitCtx dc = digit_ctx<S>(beta);
+  const int64_t total = m * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % m, c = e / m;
+    int d[S];
+    make_digits<S>(X[r + c * ldx], exps[axis == 0 ? r : c], dc, d);
+#pragma unroll
+    for (int p = 0; p < S; ++p) digits[(int64_t)p * total + e] = (uint16_t)bf16_of_int(d[p]);
+  }
+}
+
+// Expands BODY once per slice count S = 1..12 and runs the one matching `s`.
+#define BG_DISPATCH_SLICES(s, ...)               \
+  switch (s) {                                   \
+    case 1: { constexpr int S = 1; __VA_ARGS__; }       \
+    case 2: { constexpr int S = 2; __VA_ARGS__; }       \
+    case 3: { constexpr int S = 3; __VA_ARGS__; }       \
+    case 4: { constexpr int S = 4; __VA_ARGS__; }       \
+    case 5: { constexpr int S = 5; __VA_ARGS__; }       \
+    case 6: { constexpr int S = 6; __VA_ARGS__; }       \
+    case 7: { constexpr int S = 7; __VA_ARGS__; }       \
+    case 8: { constexpr int S = 8; __VA_ARGS__; }       \
+    case 9: { constexpr int S = 9; __VA_ARGS__; }       \
+    case 10: { constexpr int S = 10; __VA_ARGS__; }     \
+    case 11: { constexpr int S = 11; __VA_ARGS__; }     \
+    case 12: { constexpr int S = 12; __VA_ARGS__; }     \
+    default: return cudaErrorInvalidValue;       \
+  }
+
+}  // namespace
+
+cudaError_t launch_split_planes(int64_t m, int64_t k, const double* X, int64_t ldx, int axis,
+                                int slices, int beta_bits, int32_t* exps, uint16_t* digits,
+                                cudaStream_t st) {
+  const int64_t lines = axis == 0 ? m : k;
+  planes_exp_kernel<<<(unsigned)std::min<int64_t>((lines + 255) / 256, 4096), 256, 0, st>>>(
+      m, k, X, ldx, axis, exps);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)std::min<int64_t>((m * k + 255) / 256, 65536);
+  BG_DISPATCH_SLICES(slices, {
+    planes_digit_kernel<S><<<grid, 256, 0, st>>>(m, k, X, ldx, axis, beta_bits, exps, digits);
+    count_launch();
+    return cudaGetLastError();
+  });
+}
+
+// ---- host: plans ------------------------------------------------------------------------------
+
+int split_default_beta(int slices) { return slices <= 6 ? 8 : 7; }
+
+// Largest number of 64-wide k-blocks per FP32 accumulation for level t such
+// that every partial sum of digit products stays below 2^24 (exact in FP32).
+static bool level_chunks(int s, int beta, LevelTable* lv) {
+  memset(lv, 0, sizeof *lv);
+  for (int t = 2; t <= s + 1; ++t) {
+    double bound = 0;
+    for (int p = 1; p < t; ++p) {
+      const int q = t - p;
+      const double bp = p == 1 ? std::ldexp(1.0, beta) : std::ldexp(1.0, beta - 1);
+      const double bq = q == 1 ? std::ldexp(1.0, beta) : std::ldexp(1.0, beta - 1);
+      bound += bp * bq;
+    }
+    const double kc = std::floor(16777216.0 / (bound * BK));
+    if (kc < 1) return false;
+    lv->kcb[t] = (int8_t)std::min(kc, 100.0);
+  }
+  return true;
+}
+
+struct SplitPlan {
+  bg_dtype dt = BG_R64;
+  int s = 0, beta = 0;
+  LevelTable lv{};
+  bool chain = false;
+  int sms = 0;
+  int64_t count = 0;
+  // device
+  SliceJob* d_jobs = nullptr;
+  int64_t n_jobs = 0, n_jobs_A = 0;  // A jobs first
+  SplitUnit* d_units = nullptr;
+  int64_t n_units = 0;
+  SInst* d_inst = nullptr;       // instances (chain: walkers)
+  SInst* d_pool = nullptr;       // chain: pool entries
+  int32_t* d_order = nullptr;    // A side order (== B side order except chain)
+  int32_t* d_pool_order = nullptr;
+  int64_t* d_pool_tile0 = nullptr;
+  int32_t* d_pool_blk0 = nullptr;
+  int32_t n_pool = 0;
+  uint8_t* tilesA = nullptr;
+  uint8_t* tilesB = nullptr;
+  int32_t* metaA = nullptr;
+  int32_t* metaB = nullptr;
+  int64_t bytes = 0;
+  int grid_slice = 0, grid_gemm = 0;
+  // fixed-plan key
+  std::vector<int64_t> key;
+  std::string desc;
+};
+
+SplitWorkspace::~SplitWorkspace() {
+  for (auto* p : cache) split_plan_destroy(p);
+}
+
+static cudaError_t dalloc(void** p, size_t bytes, int64_t* total) {
+  *total += (int64_t)bytes;
+  return cudaMalloc(p, std::max<size_t>(bytes, 16));
+}
+
+template <class T>
+static cudaError_t dput(T** d, const std::vector<T>& v, int64_t* total) {
+  cudaError_t e = dalloc(reinterpret_cast<void**>(d), v.size() * sizeof(T), total);
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+void split_plan_destroy(SplitPlan* p) {
+  if (!p) return;
+  cudaFree(p->d_jobs);
+  cudaFree(p->d_units);
+  cudaFree(p->d_inst);
+  cudaFree(p->d_pool);
+  cudaFree(p->d_order);
+  cudaFree(p->d_pool_order);
+  cudaFree(p->d_pool_tile0);
+  cudaFree(p->d_pool_blk0);
+  cudaFree(p->tilesA);
+  cudaFree(p->tilesB);
+  cudaFree(p->metaA);
+  cudaFree(p->metaB);
+  delete p;
+}
+
+int64_t split_plan_workspace(const SplitPlan* p) { return p ? p->bytes : 0; }
+int split_plan_launches(const SplitPlan* p) { return p ? 2 : 0; }
+int64_t split_plan_items(const SplitPlan* p) { return p ? p->n_units : 0; }
+int split_plan_beta_bits(const SplitPlan* p) { return p ? p->beta : 0; }
+std::string split_plan_describe(const SplitPlan* p) { return p ? p->desc : "null"; }
+
+static bg_status set_err(std::string* err, bg_status s, const std::string& msg) {
+  *err = msg;
+  return s;
+}
+
+static bg_status cuda_err(std::string* err, cudaError_t e, const char* what) {
+  cudaGetLastError();
+  *err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? BG_ERR_NOMEM : BG_ERR_CUDA;
+}
+
+static bool setup_common(SplitPlan* p, bg_dtype dt, const bg_precision& pr, int sms,
+                         std::string* err) {
+  p->dt = dt;
+  p->s = pr.slices;
+  p->beta = pr.beta_bits ? pr.beta_bits : split_default_beta(pr.slices);
+  p->sms = sms;
+  if (!level_chunks(p->s, p->beta, &p->lv)) {
+    *err = "split mode: digit width too large for exact FP32 sums";
+    return false;
+  }
+  return true;
+}
+
+static int kmma_last_of(int kv) {
+  if (kv <= 0) return 0;
+  const int rem = kv - ((kv - 1) / BK) * BK;  // 1..64
+  return (rem + 15) / 16;
+}
+
+// Builds jobs and units for instances (non-chain plans).
+static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& table,
+                                 std::string* err) {
+  const bool cplx = p->dt == BG_C128;
+  const int s = p->s;
+  std::vector<SInst> inst(table.size());
+  for (size_t i = 0; i < table.size(); ++i) {
+    const bg_instance& t = table[i];
+    inst[i] = SInst{t.a_off, t.b_off, t.c_off, t.lda, t.ldb, t.ldc, (int32_t)t.m, (int32_t)t.n,
+                    (int32_t)t.k, 0};
+  }
+  // group instances of identical shape (packing needs equal shapes)
+  std::map<std::array<int64_t, 3>, std::vector<int32_t>> groups;
+  for (size_t i = 0; i < table.size(); ++i) {
+    const bg_instance& t = table[i];
+    if (t.m == 0 || t.n == 0) continue;
+    groups[{t.m, t.n, t.k}].push_back((int32_t)i);
+  }
+  std::vector<int32_t> order;
+  std::vector<SliceJob> jobsA, jobsB;
+  std::vector<SplitUnit> units;
+  int64_t tileA = 0, tileB = 0;
+  int32_t blkA = 0, blkB = 0;
+  for (auto& kv : groups) {
+    const int64_t m = kv.first[0], n = kv.first[1], k = kv.first[2];
+    const int64_t mv = cplx ? 2 * m : m, kvv = cplx ? 2 * k : k;
+    const int nkb = (int)((kvv + BK - 1) / BK);
+    const auto& ids = kv.second;
+    const bool pack = mv <= 64 && n <= 64;
+    if (pack) {
+      const int gmax = (int)std::min<int64_t>(BM / mv, BN / n);
+      for (size_t s0 = 0; s0 < ids.size(); s0 += gmax) {
+        const int gc = (int)std::min<size_t>(gmax, ids.size() - s0);
+        const int32_t pos = (int32_t)order.size();
+        for (int i = 0; i < gc; ++i) order.push_back(ids[s0 + i]);
+        SliceJob ja{tileA, blkA, pos, 0, (int16_t)gc, (int16_t)mv, (int16_t)nkb, 0, (int32_t)kvv};
+        SliceJob jb{tileB, blkB, pos, 1, (int16_t)gc, (int16_t)n, (int16_t)nkb, 0, (int32_t)kvv};
+        SplitUnit U{};
+        U.a_tile0 = tileA;
+        U.b_tile0 = tileB;
+        U.a_blk = blkA;
+        U.b_blk = blkB;
+        U.pos = pos;
+        U.g = (int16_t)gc;
+        U.nkb = (int16_t)nkb;
+        U.kmma_last = (int16_t)kmma_last_of((int)kvv);
+        U.mrow = (int16_t)mv;
+        U.ncol = (int16_t)n;
+        U.r0 = U.c0 = 0;
+        if (nkb > 0) {
+          jobsA.push_back(ja);
+          jobsB.push_back(jb);
+        }
+        units.push_back(U);
+        tileA += (int64_t)s * nkb;
+        tileB += (int64_t)s * nkb;
+        ++blkA;
+        ++blkB;
+      }
+    } else {
+      for (int32_t id : ids) {
+        const int32_t pos = (int32_t)order.size();
+        order.push_back(id);
+        const int64_t rbs = (mv + BM - 1) / BM, cbs = (n + BN - 1) / BN;
+        const int64_t tA0 = tileA, tB0 = tileB;
+        const int32_t bA0 = blkA, bB0 = blkB;
+        for (int64_t rb = 0; rb < rbs; ++rb) {
+          if (nkb > 0)
+            jobsA.push_back(SliceJob{tileA, blkA, pos, 0, 1, (int16_t)BM, (int16_t)nkb,
+                                     (int32_t)(rb * BM), (int32_t)kvv});
+          tileA += (int64_t)s * nkb;
+          ++blkA;
+        }
+        for (int64_t cb = 0; cb < cbs; ++cb) {
+          if (nkb > 0)
+            jobsB.push_back(SliceJob{tileB, blkB, pos, 1, 1, (int16_t)BN, (int16_t)nkb,
+                                     (int32_t)(cb * BN), (int32_t)kvv});
+          tileB += (int64_t)s * nkb;
+          ++blkB;
+        }
+        for (int64_t cb = 0; cb < cbs; ++cb)
+          for (int64_t rb = 0; rb < rbs; ++rb) {
+            SplitUnit U{};
+            U.a_tile0 = tA0 + rb * s * nkb;
+            U.b_tile0 = tB0 + cb * s * nkb;
+            U.a_blk = bA0 + (int32_t)rb;
+            U.b_blk = bB0 + (int32_t)cb;
+            U.pos = pos;
+            U.g = 1;
+            U.nkb = (int16_t)nkb;
+            U.kmma_last = (int16_t)kmma_last_of((int)kvv);
+            U.mrow = (int16_t)std::min<int64_t>(mv, 32767);
+            U.ncol = (int16_t)std::min<int64_t>(n, 32767);
+            U.r0 = (int32_t)(rb * BM);
+            U.c0 = (int32_t)(cb * BN);
+            units.push_back(U);
+          }
+      }
+    }
+  }
+  // longest first
+  std::stable_sort(units.begin(), units.end(),
+                   [](const SplitUnit& a, const SplitUnit& b) { return a.nkb > b.nkb; });
+  std::stable_sort(jobsA.begin(), jobsA.end(),
+                   [](const SliceJob& a, const SliceJob& b) { return a.nkb > b.nkb; });
+  std::stable_sort(jobsB.begin(), jobsB.end(),
+                   [](const SliceJob& a, const SliceJob& b) { return a.nkb > b.nkb; });
+  std::vector<SliceJob> jobs;
+  // interleave A and B jobs so both sides progress together
+  size_t ia = 0, ib = 0;
+  while (ia < jobsA.size() || ib < jobsB.size()) {
+    if (ia < jobsA.size()) jobs.push_back(jobsA[ia++]);
+    if (ib < jobsB.size()) jobs.push_back(jobsB[ib++]);
+  }
+  p->n_jobs = (int64_t)jobs.size();
+  p->n_jobs_A = (int64_t)jobsA.size();
+  p->n_units = (int64_t)units.size();
+  p->count = (int64_t)table.size();
+  cudaError_t e;
+  if ((e = dput(&p->d_jobs, jobs, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_units, units, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_inst, inst, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_order, order, &p->bytes)) != cudaSuccess ||
+      (e = dalloc(reinterpret_cast<void**>(&p->tilesA), (size_t)tileA * kTileBytes, &p->bytes)) !=
+          cudaSuccess ||
+      (e = dalloc(reinterpret_cast<void**>(&p->tilesB), (size_t)tileB * kTileBytes, &p->bytes)) !=
+          cudaSuccess ||
+      (e = dalloc(reinterpret_cast<void**>(&p->metaA), (size_t)std::max(blkA, 1) * kMetaStride * 4,
+                  &p->bytes)) != cudaSuccess ||
+      (e = dalloc(reinterpret_cast<void**>(&p->metaB), (size_t)std::max(blkB, 1) * kMetaStride * 4,
+                  &p->bytes)) != cudaSuccess)
+    return cuda_err(err, e, "split plan allocation");
+  // meta of blocks without slice jobs (k == 0) must read as zero lines
+  if ((e = cudaMemset(p->metaA, 0, (size_t)std::max(blkA, 1) * kMetaStride * 4)) != cudaSuccess ||
+      (e = cudaMemset(p->metaB, 0, (size_t)std::max(blkB, 1) * kMetaStride * 4)) != cudaSuccess)
+    return cuda_err(err, e, "split plan meta clear");
+  return BG_OK;
+}
+
+static void finish_desc(SplitPlan* p) {
+  char buf[512];
+  std::string kc;
+  for (int t = 2; t <= p->s + 1; ++t) kc += (t > 2 ? "," : "") + std::to_string(p->lv.kcb[t]);
+  snprintf(buf, sizeof buf,
+           "{\"slices\": %d, \"beta_bits\": %d, \"pairs\": %d, \"level_chunk_kblocks\": [%s], "
+           "\"units\": %lld, \"slice_jobs\": %lld, \"tile\": [%d, %d, %d], \"stages\": %d, "
+           "\"workspace_bytes\": %lld}",
+           p->s, p->beta, p->s * (p->s + 1) / 2, kc.c_str(), (long long)p->n_units,
+           (long long)p->n_jobs, BM, BN, BK, kStages, (long long)p->bytes);
+  p->desc = buf;
+}
+
+static void grids(SplitPlan* p) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kGemmSmemBytes);
+    attr_set = true;
+  }
+  p->grid_gemm = (int)std::max<int64_t>(1, std::min<int64_t>(p->sms, p->n_units));
+  int bps = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, split_slice_kernel<9>, kSliceThreads, 0);
+  if (bps < 1) bps = 1;
+  p->grid_slice = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)p->sms * bps, p->n_jobs));
+}
+
+bg_status split_plan_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr,
+                            const std::vector<bg_instance>& table, const int64_t* d_table,
+                            int sms, bool autotune, cudaStream_t st, std::string* err) {
+  (void)d_table;
+  (void)autotune;
+  (void)st;
+  SplitPlan* p = new SplitPlan();
+  if (!setup_common(p, dt, pr, sms, err)) {
+    delete p;
+    return BG_ERR_INVALID_ARG;
+  }
+  bg_status s = build_instances(p, table, err);
+  if (s != BG_OK) {
+    split_plan_destroy(p);
+    return s;
+  }
+  grids(p);
+  finish_desc(p);
+  *out = p;
+  return BG_OK;
+}
+
+static cudaError_t launch_slicer(SplitPlan* p, const SliceJob* jobs, int64_t njobs,
+                                 const SInst* instA, const SInst* instB, const int32_t* orderA,
+                                 const int32_t* orderB, const void* A, const void* B,
+                                 cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  SliceArgs a;
+  a.jobs = jobs;
+  a.njobs = njobs;
+  a.instA = instA;
+  a.instB = instB;
+  a.orderA = orderA;
+  a.orderB = orderB;
+  a.A = static_cast<const double*>(A);
+  a.B = static_cast<const double*>(B);
+  a.tilesA = p->tilesA;
+  a.tilesB = p->tilesB;
+  a.metaA = p->metaA;
+  a.metaB = p->metaB;
+  a.cplx = p->dt == BG_C128;
+  a.s = p->s;
+  a.beta = p->beta;
+  const int grid = (int)std::min<int64_t>(p->grid_slice, njobs);
+  BG_DISPATCH_SLICES(p->s, {
+    split_slice_kernel<S><<<grid, kSliceThreads, 0, st>>>(a);
+    count_launch();
+    return cudaGetLastError();
+  });
+}
+
+static cudaError_t launch_gemm(SplitPlan* p, void* C, const Scalars& sc, const int32_t* idx,
+                               int* d_err, cudaStream_t st) {
+  if (p->n_units <= 0) return cudaSuccess;
+  GemmArgs g;
+  g.units = p->d_units;
+  g.nunits = p->n_units;
+  g.inst = p->d_inst;
+  g.order = p->d_order;
+  g.tilesA = p->tilesA;
+  g.tilesB = p->tilesB;
+  g.metaA = p->metaA;
+  g.metaB = p->metaB;
+  g.C = static_cast<double*>(C);
+  g.idx = idx;
+  g.pool_tile0 = p->d_pool_tile0;
+  g.pool_blk0 = p->d_pool_blk0;
+  g.pool = p->d_pool;
+  g.pool_count = p->n_pool;
+  g.sc = sc;
+  g.cplx = p->dt == BG_C128;
+  g.s = p->s;
+  g.beta = p->beta;
+  g.skip_product = sc.alpha_zero;
+  g.lv = p->lv;
+  g.err = d_err;
+  split_gemm_kernel<<<p->grid_gemm, kGemmThreads, kGemmSmemBytes, st>>>(g);
+  count_launch();
+  return cudaGetLastError();
+}
+
+bg_status split_plan_run(SplitPlan* p, const void* A, const void* B, void* C, const Scalars& s,
+                         int* d_err, cudaStream_t st, std::string* err, cudaEvent_t* ev) {
+  cudaError_t e;
+  if (!s.alpha_zero) {
+    e = launch_slicer(p, p->d_jobs, p->n_jobs, p->d_inst, p->d_inst, p->d_order, p->d_order, A, B,
+                      st);
+    if (e != cudaSuccess) return cuda_err(err, e, "split slicer launch");
+  }
+  if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return cuda_err(err, e, "event");
+  e = launch_gemm(p, C, s, nullptr, d_err, st);
+  if (e != cudaSuccess) return cuda_err(err, e, "split GEMM launch");
+  if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return cuda_err(err, e, "event");
+  return BG_OK;
+}
+
+bg_status split_fixed(bg_dtype dt, const bg_precision& pr, int64_t m, int64_t n, int64_t k,
+                      const Scalars& s, const void* A, int64_t lda, int64_t sA, const void* B,
+                      int64_t ldb, int64_t sB, void* C, int64_t ldc, int64_t sC, int64_t batch,
+                      SplitWorkspace* ws, int sms, int* d_err, bool capturing, cudaStream_t st,
+                      std::string* err) {
+  const int beta = pr.beta_bits ? pr.beta_bits : split_default_beta(pr.slices);
+  std::vector<int64_t> key = {(int64_t)dt, m, n, k, lda, ldb, ldc, sA, sB, sC, batch,
+                              pr.slices, beta};
+  SplitPlan* p = nullptr;
+  for (size_t i = 0; i < ws->cache.size(); ++i)
+    if (ws->cache[i]->key == key) {
+      p = ws->cache[i];
+      ws->cache.erase(ws->cache.begin() + i);
+      ws->cache.push_back(p);
+      break;
+    }
+  if (!p) {
+    if (capturing)
+      return set_err(err, BG_ERR_CAPTURE,
+                     "first split-mode call of this shape allocates its workspace; the stream "
+                     "is being captured");
+    std::vector<bg_instance> table((size_t)batch);
+    for (int64_t i = 0; i < batch; ++i)
+      table[i] = bg_instance{m, n, k, lda, ldb, ldc, i * sA, i * sB, i * sC};
+    bg_status rs = split_plan_create(&p, dt, pr, table, nullptr, sms, false, st, err);
+    if (rs != BG_OK) return rs;
+    p->key = key;
+    ws->cache.push_back(p);
+    while (ws->cache.size() > 4) {
+      // the oldest plan may still be in use by queued work: wait before freeing
+      cudaDeviceSynchronize();
+      split_plan_destroy(ws->cache.front());
+      ws->cache.erase(ws->cache.begin());
+    }
+  }
+  return split_plan_run(p, A, B, C, s, d_err, st, err);
+}
+
+// ---- chain plans -----------------------------------------------------------------------------
+
+bg_status split_chain_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr,
+                             const std::vector<int64_t>& wn, const std::vector<int64_t>& woff,
+                             const std::vector<int64_t>& pool_n,
+                             const std::vector<int64_t>& pool_off, int sms, cudaStream_t st,
+                             std::string* err) {
+  (void)st;
+  SplitPlan* p = new SplitPlan();
+  if (!setup_common(p, dt, pr, sms, err)) {
+    delete p;
+    return BG_ERR_INVALID_ARG;
+  }
+  p->chain = true;
+  const bool cplx = dt == BG_C128;
+  const int s = p->s;
+  // pool entries: A blocks (row blocks), sliced once per chain_step call
+  std::vector<SInst> pool(pool_n.size());
+  std::vector<int32_t> pool_order(pool_n.size());
+  std::vector<int64_t> pool_tile0(pool_n.size());
+  std::vector<int32_t> pool_blk0(pool_n.size());
+  std::vector<SliceJob> jobsA;
+  int64_t tileA = 0;
+  int32_t blkA = 0;
+  for (size_t j = 0; j < pool_n.size(); ++j) {
+    const int64_t n = pool_n[j];
+    pool[j] = SInst{pool_off[j], 0, 0, std::max<int64_t>(1, n), 1, 1, (int32_t)n, (int32_t)n,
+                    (int32_t)n, 0};
+    pool_order[j] = (int32_t)j;
+    const int64_t mv = cplx ? 2 * n : n, kvv = mv;
+    const int nkb = (int)((kvv + BK - 1) / BK);
+    pool_tile0[j] = tileA;
+    pool_blk0[j] = blkA;
+    for (int64_t rb = 0; rb < (mv + BM - 1) / BM; ++rb) {
+      if (nkb > 0)
+        jobsA.push_back(SliceJob{tileA, blkA, (int32_t)j, 0, 1, (int16_t)BM, (int16_t)nkb,
+                                 (int32_t)(rb * BM), (int32_t)kvv});
+      tileA += (int64_t)s * nkb;
+      ++blkA;
+    }
+  }
+  // walkers: B blocks (column blocks of the state), sliced every step
+  std::vector<SInst> inst(wn.size());
+  std::vector<int32_t> order(wn.size());
+  std::vector<SliceJob> jobsB;
+  std::vector<SplitUnit> units;
+  int64_t tileB = 0;
+  int32_t blkB = 0;
+  for (size_t w = 0; w < wn.size(); ++w) {
+    const int64_t n = wn[w];
+    inst[w] = SInst{0, woff[w], woff[w], std::max<int64_t>(1, n), std::max<int64_t>(1, n),
+                    std::max<int64_t>(1, n), (int32_t)n, (int32_t)n, (int32_t)n, 0};
+    order[w] = (int32_t)w;
+    if (n == 0) continue;
+    const int64_t mv = cplx ? 2 * n : n, kvv = mv;
+    const int nkb = (int)((kvv + BK - 1) / BK);
+    const int64_t rbs = (mv + BM - 1) / BM, cbs = (n + BN - 1) / BN;
+    const int64_t tB0 = tileB;
+    const int32_t bB0 = blkB;
+    for (int64_t cb = 0; cb < cbs; ++cb) {
+      jobsB.push_back(SliceJob{tileB, blkB, (int32_t)w, 1, 1, (int16_t)BN, (int16_t)nkb,
+                               (int32_t)(cb * BN), (int32_t)kvv});
+      tileB += (int64_t)s * nkb;
+      ++blkB;
+    }
+    for (int64_t cb = 0; cb < cbs; ++cb)
+      for (int64_t rb = 0; rb < rbs; ++rb) {
+        SplitUnit U{};
+        U.a_tile0 = rb * s * nkb;  // relative to the pool entry's first tile
+        U.b_tile0 = tB0 + cb * s * nkb;
+        U.a_blk = (int32_t)rb;     // relative to the pool entry's first block
+        U.b_blk = bB0 + (int32_t)cb;
+        U.pos = (int32_t)w;
+        U.g = 1;
+        U.nkb = (int16_t)nkb;
+        U.kmma_last = (int16_t)kmma_last_of((int)kvv);
+        U.mrow = (int16_t)std::min<int64_t>(mv, 32767);
+        U.ncol = (int16_t)std::min<int64_t>(n, 32767);
+        U.r0 = (int32_t)(rb * BM);
+        U.c0 = (int32_t)(cb * BN);
+        units.push_back(U);
+      }
+  }
+  std::stable_sort(units.begin(), units.end(),
+                   [](const SplitUnit& a, const SplitUnit& b) { return a.nkb > b.nkb; });
+  std::vector<SliceJob> jobs = jobsA;  // pool jobs first, then walker jobs
+  jobs.insert(jobs.end(), jobsB.begin(), jobsB.end());
+  p->n_jobs = (int64_t)jobs.size();
+  p->n_jobs_A = (int64_t)jobsA.size();
+  p->n_units = (int64_t)units.size();
+  p->count = (int64_t)wn.size();
+  p->n_pool = (int32_t)pool_n.size();
+  cudaError_t e;
+  if ((e = dput(&p->d_jobs, jobs, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_units, units, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_inst, inst, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_pool, pool, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_order, order, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_pool_order, pool_order, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_pool_tile0, pool_tile0, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_pool_blk0, pool_blk0, &p->bytes)) != cudaSuccess ||
+      (e = dalloc(reinterpret_cast<void**>(&p->tilesA), (size_t)tileA * kTileBytes, &p->bytes)) !=
+          cudaSuccess ||
+      (e = dalloc(reinterpret_cast<void**>(&p->tilesB), (size_t)tileB * kTileBytes, &p->bytes)) !=
+          cudaSuccess ||
+      (e = dalloc(reinterpret_cast<void**>(&p->metaA), (size_t)std::max(blkA, 1) * kMetaStride * 4,
+                  &p->bytes)) != cudaSuccess ||
+      (e = dalloc(reinterpret_cast<void**>(&p->metaB), (size_t)std::max(blkB, 1) * kMetaStride * 4,
+                  &p->bytes)) != cudaSuccess) {
+    bg_status rs = cuda_err(err, e, "split chain plan allocation");
+    split_plan_destroy(p);
+    return rs;
+  }
+  cudaMemset(p->metaA, 0, (size_t)std::max(blkA, 1) * kMetaStride * 4);
+  cudaMemset(p->metaB, 0, (size_t)std::max(blkB, 1) * kMetaStride * 4);
+  grids(p);
+  finish_desc(p);
+  *out = p;
+  return BG_OK;
+}
+
+bg_status split_chain_prepare_pool(SplitPlan* p, const void* U, int* d_err, cudaStream_t st,
+                                   std::string* err) {
+  (void)d_err;
+  cudaError_t e = launch_slicer(p, p->d_jobs, p->n_jobs_A, p->d_pool, p->d_inst, p->d_pool_order,
+                                p->d_order, U, nullptr, st);
+  if (e != cudaSuccess) return cuda_err(err, e, "split pool slicer launch");
+  return BG_OK;
+}
+
+bg_status split_chain_step(SplitPlan* p, const void* U, const int32_t* idx_row, const void* Cin,
+                           void* Cout, int* d_err, cudaStream_t st, std::string* err) {
+  (void)U;
+  cudaError_t e = launch_slicer(p, p->d_jobs + p->n_jobs_A, p->n_jobs - p->n_jobs_A, p->d_pool,
+                                p->d_inst, p->d_pool_order, p->d_order, nullptr, Cin, st);
+  if (e != cudaSuccess) return cuda_err(err, e, "split state slicer launch");
+  Scalars sc;
+  sc.alpha_re = 1.0;
+  sc.alpha_im = 0.0;
+  sc.beta_re = 0.0;
+  sc.beta_im = 0.0;
+  sc.alpha_zero = 0;
+  sc.beta_zero = 1;
+  e = launch_gemm(p, Cout, sc, idx_row, d_err, st);
+  if (e != cudaSuccess) return cuda_err(err, e, "split chain GEMM launch");
+  return BG_OK;
+}
+
+}  // namespace bg

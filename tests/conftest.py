@@ -35,3 +35,21 @@ def rel_err_instances(batch, C_test, C_ref):
         num = np.linalg.norm(ct - cr)
         out[i] = num / den if den > 0 else num
     return out
+
+
+@pytest.fixture(scope="session")
+def bglib():
+    """The built C-ABI library (compiled here with nvcc when missing or stale)."""
+    from paper_2203_09353_gb300 import build
+    build.build()
+    import paper_2203_09353_gb300 as bg
+    return bg.load_library()
+
+
+@pytest.fixture(scope="session")
+def gpu(bglib):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    return torch.device("cuda:0")

@@ -1,0 +1,214 @@
+"""GPU parity of the split-BF16 tensor-core mode against the FP64 oracle.
+
+Tolerances (per instance, ||C - C_ref||_F / (||A||_F ||B||_F)): 1e-6 for the
+3-slice mode, 1e-12 for the 6- and 9-slice modes. Exactness pins: inputs that
+the digit planes represent exactly (small integers times powers of two) must
+give the exact product bit for bit, which checks that the FP32 tensor-core
+sums and the integer recombination lose nothing.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2203_09353_gb300 as bg
+from paper_2203_09353_gb300 import synth
+
+from gpu_util import TOL_FP64, TOL_SPLIT, dev, errors, host, oracle_batch, run_fixed, run_grouped
+
+pytestmark = pytest.mark.gpu
+
+
+def split(s, beta_bits=0):
+    return bg.precision("split", s, beta_bits)
+
+
+@pytest.mark.parametrize("s", [3, 6, 9])
+def test_config4_size_mix_reduced(gpu, s):
+    """Log-uniform entries (1e-4..1e4, random signs), all six size classes, alpha=1, beta=0.5."""
+    b = synth.config4(count=150)
+    C, plan = run_grouped(b, split(s))
+    info = plan.info()
+    assert info["slices"] == s and info["launches_per_call"] == 2
+    e = errors(b, host(C), oracle_batch(b))
+    assert e.max() <= TOL_SPLIT[s], (s, e.max())
+
+
+@pytest.mark.parametrize("s", [3, 6, 9])
+def test_config3_uniform_reduced(gpu, s):
+    b = synth.config3(count=120)
+    C, _ = run_grouped(b, split(s))
+    e = errors(b, host(C), oracle_batch(b))
+    assert e.max() <= TOL_SPLIT[s], (s, e.max())
+
+
+def test_error_decreases_with_slices(gpu):
+    b = synth.config4(count=100)
+    ref = oracle_batch(b)
+    prev = np.inf
+    for s in (2, 3, 4, 6, 8, 9):
+        C, _ = run_grouped(b, split(s))
+        e = errors(b, host(C), ref).max()
+        assert e <= prev * 1.0001 + 1e-17, (s, e, prev)
+        prev = e
+    assert prev <= 1e-14
+
+
+def test_nine_slices_within_fp64_envelope(gpu):
+    """9-slice error is of the order of the plain FP64 path's error."""
+    b = synth.config4(count=100)
+    ref = oracle_batch(b)
+    C64, _ = run_grouped(b)
+    C9, _ = run_grouped(b, split(9))
+    e64 = errors(b, host(C64), ref)
+    e9 = errors(b, host(C9), ref)
+    assert e9.max() <= max(8 * e64.max(), 4e-16), (e9.max(), e64.max())
+
+
+@pytest.mark.parametrize("dtype", ["r64", "c128"])
+@pytest.mark.parametrize("n", [16, 48, 64, 130, 256])
+def test_exact_on_representable_inputs(gpu, dtype, n):
+    """Entries d * 2^j with |d| < 2^7 are cut exactly into 3 planes; every product
+    and sum then fits FP64 exactly, so the result must equal the oracle bit for bit."""
+    rng = np.random.default_rng(n)
+    count = 6
+    shapes = [(n, n, n)] * count
+    table, la, lb, lc = synth.pack_table(shapes)
+
+    def fill(size):
+        v = rng.integers(-127, 128, size).astype(np.float64)
+        if dtype == "c128":
+            v = v + 1j * rng.integers(-127, 128, size)
+        return v
+
+    # per row of A a common power of two; per column of B too (exactly representable)
+    A, B, C = fill(la), fill(lb), np.zeros(lc, dtype=np.complex128 if dtype == "c128" else np.float64)
+    for i in range(count):
+        ao, bo = table[i, 6], table[i, 7]
+        a = A[ao:ao + n * n].reshape(n, n).T
+        a *= (2.0 ** rng.integers(-20, 20, n))[:, None]
+        A[ao:ao + n * n] = a.T.ravel()
+        bb = B[bo:bo + n * n].reshape(n, n).T
+        bb *= (2.0 ** rng.integers(-20, 20, n))[None, :]
+        B[bo:bo + n * n] = bb.T.ravel()
+    b = synth.Batch("exact", dtype, table, A, B, C, 1.0, 0.0)
+    Cg, _ = run_grouped(b, split(3, 8))
+    assert np.array_equal(host(Cg), oracle_batch(b))
+
+
+@pytest.mark.parametrize("dtype", ["r64", "c128"])
+def test_fixed_split_modes(gpu, dtype):
+    b = synth.fixed_uniform(40, 33, 47, 61, seed=12, dtype=dtype,
+                            alpha=(0.5 + 1j) if dtype == "c128" else 0.5,
+                            beta=(0.25 - 1j) if dtype == "c128" else 0.25)
+    ref = oracle_batch(b)
+    for s in (3, 6, 9):
+        C = host(run_fixed(b, split(s)))
+        e = errors(b, C, ref)
+        assert e.max() <= TOL_SPLIT[s], (s, e.max())
+
+
+def test_config2_complex_split_reduced(gpu):
+    b = synth.config2(batch=64)
+    ref = oracle_batch(b)
+    for s in (3, 6, 9):
+        C = host(run_fixed(b, split(s)))
+        e = errors(b, C, ref)
+        assert e.max() <= TOL_SPLIT[s], (s, e.max())
+
+
+@pytest.mark.parametrize("dtype", ["r64", "c128"])
+def test_split_ragged_shapes_and_zero_k(gpu, dtype):
+    rng = np.random.default_rng(8)
+    shapes = [(int(rng.integers(1, 150)), int(rng.integers(1, 150)), int(rng.integers(0, 150)))
+              for _ in range(30)] + [(5, 5, 0), (64, 64, 64), (20, 20, 20), (20, 20, 20)]
+    table, la, lb, lc = synth.pack_table(shapes)
+    dt = np.complex128 if dtype == "c128" else np.float64
+
+    def fill(size):
+        x = rng.uniform(-1, 1, size)
+        return (x + 1j * rng.uniform(-1, 1, size)).astype(dt) if dtype == "c128" else x
+
+    b = synth.Batch("ragged", dtype, table, fill(la), fill(lb), fill(lc),
+                    (1 + 1j) if dtype == "c128" else 2.0, (0.5 - 0.5j) if dtype == "c128" else -0.5)
+    ref = oracle_batch(b)
+    for s in (3, 9):
+        C, _ = run_grouped(b, split(s))
+        e = errors(b, host(C), ref)
+        assert e.max() <= TOL_SPLIT[s], (s, e.max())
+
+
+def test_split_alpha_zero_and_nan_c(gpu):
+    b = synth.config4(count=40)
+    plan = bg.batched_gemm_plan("r64", b.table, split(6))
+    An, Bn = dev(np.full_like(b.A, np.nan)), dev(np.full_like(b.B, np.nan))
+    Cd = dev(b.C)
+    bg.batched_gemm_grouped(plan, An, Bn, Cd, 0.0, 2.0)
+    assert np.array_equal(host(Cd), 2.0 * b.C)
+    b0 = synth.Batch(b.name, b.dtype, b.table, b.A, b.B, np.full_like(b.C, np.nan), 1.0, 0.0)
+    Cd = dev(b0.C)
+    bg.batched_gemm_grouped(plan, dev(b.A), dev(b.B), Cd, 1.0, 0.0)
+    got = host(Cd)
+    live = np.zeros(b.C.size, dtype=bool)
+    for i in range(b.count):
+        m, n, _, _, _, ldc, _, _, co = b.table[i]
+        for j in range(n):
+            live[co + j * ldc: co + j * ldc + m] = True
+    assert np.all(np.isfinite(got[live]))
+    e = errors(b0, got, oracle_batch(b0, C0=np.zeros_like(b.C)))
+    assert e.max() <= TOL_SPLIT[6]
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("s,beta", [(3, 8), (6, 7), (9, 7), (4, 5)])
+def test_planes_reconstruct_input(gpu, axis, s, beta):
+    """sum_p d_p 2^(e - beta p) equals the input to half a unit of the last digit; digits
+    are integers within their bounds; the line exponent bounds the line's magnitudes."""
+    import torch
+    rng = np.random.default_rng(s * 10 + beta + axis)
+    m, k = 37, 53
+    X = rng.uniform(-1, 1, (m, k)) * 10.0 ** rng.uniform(-6, 6, (m, k))
+    X[3, :] = 0.0
+    X[:, 5] = 0.0
+    Xf = np.asfortranarray(X)
+    lines = m if axis == 0 else k
+    exps = torch.zeros(lines, dtype=torch.int32, device="cuda")
+    digits = torch.zeros(s * m * k, dtype=torch.int16, device="cuda")
+    bg.split_planes(m, k, dev(Xf.ravel(order="F")), m, axis, s, beta, exps, digits)
+    e = host(exps).astype(np.int64)
+    raw = host(digits).view(np.uint16).astype(np.uint32) << 16
+    dv = raw.view(np.float32).astype(np.float64).reshape(s, k, m).transpose(0, 2, 1)
+    assert np.all(dv == np.round(dv))
+    assert np.all(np.abs(dv[0]) <= 2.0 ** beta)
+    assert np.all(np.abs(dv[1:]) <= 2.0 ** (beta - 1))
+    for l in range(lines):
+        line = X[l, :] if axis == 0 else X[:, l]
+        if np.all(line == 0):
+            assert e[l] == 0
+        else:
+            assert np.max(np.abs(line)) < 2.0 ** e[l] <= 2 * np.max(np.abs(line))
+    E = e[:, None] if axis == 0 else e[None, :]
+    recon = np.zeros((m, k))
+    for p in range(s):
+        recon += dv[p] * np.ldexp(1.0, (E - beta * (p + 1)).astype(np.int64))
+    ulp_last = np.ldexp(1.0, (E - beta * s).astype(np.int64))
+    assert np.all(np.abs(recon - X) <= 0.5 * ulp_last * (1 + 1e-12))
+
+
+def test_bounded_wait_reports_timeout(gpu):
+    bg.check_device_errors()
+    bg.test_bounded_wait(2000)
+    with pytest.raises(bg.BgemmError) as ei:
+        bg.check_device_errors()
+    assert ei.value.status == 6
+    bg.check_device_errors()  # cleared
+
+
+def test_split_runs_leave_no_device_error(gpu):
+    b = synth.config4(count=30)
+    run_grouped(b, split(9))
+    bg.check_device_errors()
+
+
+def test_fp64_peak_probe(gpu):
+    t = bg.probe_fp64_peak()
+    assert 0.1 < t < 100.0

@@ -207,6 +207,14 @@ class Clocks:
                 "power_w_max": float(np.nanmax(power))}
 
 
+_T0 = time.time()
+
+
+def log(msg: str) -> None:
+    sys.stderr.write(f"[bench {time.time() - _T0:7.1f}s] {msg}\n")
+    sys.stderr.flush()
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -285,6 +293,7 @@ def main():
     stream = torch.cuda.current_stream()
     pk, pk_src = peaks()
     batch, desc = make_batch(args.config, args.count, rank)
+    log(f"generated {desc}")
     flops = batch.flops()
     A = torch.from_numpy(batch.A).to(dev)
     B = torch.from_numpy(batch.B).to(dev)
@@ -295,6 +304,7 @@ def main():
         modes.append(args.mode)
 
     fp64_peak = bg.probe_fp64_peak()
+    log(f"FP64 DFMA probe: {fp64_peak:.3f} TFLOP/s")
     cache = os.path.join(tempfile.gettempdir(), "bgemm_autotune.json")
     plans = {}
     for m in modes:
@@ -304,6 +314,8 @@ def main():
             prec, flags = bg.precision("split", int(m[5:])), bg.BG_PLAN_PROFILE
         plans[m] = bg.batched_gemm_plan(batch.dtype, batch.table, prec, flags, cache)
 
+    log("plans built: " + ", ".join(f"{m}: {plans[m].info()['workspace_bytes'] / 2**30:.2f} GiB"
+                                    for m in modes))
     # --- correctness of every mode: oracle on a sample (rank 0), FP64 path on all instances
     ref, cpu = None, None
     if rank == 0 and not args.no_cpu:
@@ -313,6 +325,7 @@ def main():
                "sample": (f"{len(ids)} of {batch.count} instances (every "
                           f"{max(1, batch.count // max(1, len(ids)))}-th, all size classes), "
                           f"{fl / 1e9:.2f} GFLOP in {dt:.2f} s")}
+        log(f"oracle sample: {cpu['sample']}")
     outs = {}
     for m in modes:
         Cm = C0.clone()
@@ -331,6 +344,7 @@ def main():
             e["max_vs_fp64_path_all"] = float(errbuf.max().item())
         errs[m] = e
     del outs
+    log("errors: " + json.dumps(errs))
 
     # --- timing per mode
     res = {}
@@ -363,6 +377,7 @@ def main():
         ms = e0.elapsed_time(e1) / steps
         ms = max_over_ranks(pg, ms)
         kt, calls = plans[m].kernel_times(reset=True)
+        log(f"{m}: {ms:.3f} ms/step")
         res[m] = {"ms_per_step": ms, "steps": steps,
                   "value": flops * world / (ms * 1e-3) / 1e12,
                   "kernel_ms": [kt[0] / max(calls, 1), kt[1] / max(calls, 1)]}

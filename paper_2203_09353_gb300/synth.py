@@ -22,9 +22,11 @@ sizes), one recipe per benchmark configuration:
   [steps, walkers] pool-index table and a Haar-unitary start state per walker.
 
 Draw order (fixed so that every run sees the same numbers): sizes first
-(``rng.choice``), then per instance in table order A, B, C, each filled in
-column-major order; a log-uniform matrix draws its magnitudes before its
-signs; a complex Gaussian draws its real part before its imaginary part.
+(``rng.choice``); then for a grouped batch the whole packed A array in one
+draw (instances in table order, each column-major), then all of B, then all
+of C; a log-uniform array draws all its magnitudes, then its signs (as random
+bits); a complex Gaussian draws its real part before its imaginary part.
+Alignment gaps between packed instances are zero.
 
 Memory layout of a batch: every instance is column-major and packed
 back-to-back in three flat arrays (A, B, C) at offsets that are multiples of
@@ -120,11 +122,19 @@ def _uniform(rng, out: np.ndarray) -> None:
     out -= 1.0
 
 
+_LOG2_10 = float(np.log2(10.0))
+
+
 def _log_uniform_signed(rng, size: int) -> np.ndarray:
-    """Magnitude 10^U(-4, 4) with a random sign (p = 1/2)."""
-    mag = 10.0 ** (rng.random(size) * 8.0 - 4.0)
-    sign = np.where(rng.random(size) < 0.5, -1.0, 1.0)
-    return mag * sign
+    """Magnitude 10^U(-4, 4) = 2^(log2(10) (8u - 4)) with a random sign (p = 1/2):
+    magnitudes first, then sign bits."""
+    x = rng.random(size)
+    x *= 8.0 * _LOG2_10
+    x -= 4.0 * _LOG2_10
+    np.exp2(x, out=x)
+    bits = np.unpackbits(rng.integers(0, 256, (size + 7) // 8, dtype=np.uint8))[:size]
+    np.negative(x, out=x, where=bits.view(bool))
+    return x
 
 
 def complex_gaussian(rng, shape) -> np.ndarray:
@@ -199,6 +209,19 @@ def draw_sizes(rng, count: int, sizes=CONFIG3_SIZES, weights=CONFIG3_WEIGHTS) ->
     return rng.choice(np.asarray(sizes, dtype=np.int64), size=count, p=np.asarray(weights))
 
 
+def _gap_mask(table: np.ndarray, length: int, rows: int, cols: int, ld: int, off: int):
+    """Boolean mask of the elements that belong to some instance of a packed array."""
+    keep = np.zeros(length, dtype=bool)
+    for t in table:
+        r, c, l, o = int(t[rows]), int(t[cols]), int(t[ld]), int(t[off])
+        if r == l:
+            keep[o:o + r * c] = True
+        else:
+            for j in range(c):
+                keep[o + j * l:o + j * l + r] = True
+    return keep
+
+
 def mixed_batch(seed: int, count: int, values: str, alpha=1.0, beta=0.5, sizes=CONFIG3_SIZES,
                 weights=CONFIG3_WEIGHTS, name: str | None = None) -> Batch:
     """Grouped real batch of square instances with sizes drawn from ``sizes``.
@@ -208,14 +231,19 @@ def mixed_batch(seed: int, count: int, values: str, alpha=1.0, beta=0.5, sizes=C
     rng = np.random.default_rng(seed)
     ns = draw_sizes(rng, count, sizes, weights)
     table, la, lb, lc = pack_table([(int(n), int(n), int(n)) for n in ns])
-    A, B, C = (np.zeros(x, dtype=np.float64) for x in (la, lb, lc))
-    for i in range(count):
-        n = int(ns[i])
-        for X, off in ((A, table[i, 6]), (B, table[i, 7]), (C, table[i, 8])):
-            if values == "uniform":
-                _uniform(rng, X[off:off + n * n])
-            else:
-                X[off:off + n * n] = _log_uniform_signed(rng, n * n)
+    out = []
+    for length, (rows, cols, ld, off) in ((la, (0, 2, 3, 6)), (lb, (2, 1, 4, 7)),
+                                          (lc, (0, 1, 5, 8))):
+        if values == "uniform":
+            X = np.empty(length)
+            _uniform(rng, X)
+        else:
+            X = _log_uniform_signed(rng, length)
+        dense = int(np.sum(table[:, rows] * table[:, cols]))
+        if dense != length:
+            X[~_gap_mask(table, length, rows, cols, ld, off)] = 0.0
+        out.append(X)
+    A, B, C = out
     return Batch(name or f"mixed_{values}_{count}_seed{seed}", "r64", table, A, B, C, alpha,
                  beta, meta={"sizes": ns})
 

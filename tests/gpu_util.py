@@ -62,8 +62,9 @@ def run_fixed(batch, prec=None, C=None):
     m, n, k, count = batch.fixed_shape()
     A, B = dev(batch.A), dev(batch.B)
     Cd = dev(batch.C if C is None else C)
-    bg.batched_gemm_fixed(batch.dtype, m, n, k, batch.alpha, A, m, m * k, B, k, k * n,
-                          batch.beta, Cd, m, m * n, count, prec)
+    lda, ldb, ldc = max(m, 1), max(k, 1), max(m, 1)
+    bg.batched_gemm_fixed(batch.dtype, m, n, k, batch.alpha, A, lda, m * k, B, ldb, k * n,
+                          batch.beta, Cd, ldc, m * n, count, prec)
     return Cd
 
 

@@ -15,10 +15,10 @@
 //     (p >= 2). Every digit is an integer of at most 9 significant bits, hence
 //     exact in BF16. Same for B per column.
 //  3. Multiply. For each level t = p + q (2 <= t <= s+1, the triangular set of
-//     plane pairs), L_t = sum_{p+q=t} D_p^A D_q^B on the tensor cores. K is cut
-//     into chunks small enough that every partial sum stays below 2^24, so the
-//     FP32 accumulation is exact; the chunk size per level follows from the
-//     digit bounds (host: level_chunks()).
+//     plane pairs), L_t = sum_{p+q=t} D_p^A D_q^B on the tensor cores. The digit
+//     width is chosen (host: level_pass()) so that every partial sum of a level
+//     stays below 2^24 over a pass of k: the FP32 accumulation is exact; longer
+//     k runs in several passes whose FP64 results are summed into C.
 //  4. Recombine. G_ij = sum_t L_t 2^(-beta (t-2)) is accumulated per element in
 //     a 64-bit fixed-point integer whose frame is set from bounds on the row and
 //     column digit norms (so it cannot overflow and keeps >= 60 bits of the
@@ -32,16 +32,24 @@
 // real and imaginary parts of a row of A / a column of B.
 //
 // Kernels:
-//  * split_slice_kernel: one CTA per 128-line block of A (rows) or B (columns):
-//    exponents, digit planes written as pre-swizzled 128 x 64 BF16 tiles
-//    (the exact SWIZZLE_128B K-major shared-memory image), per-line norm
-//    exponents. Integer arithmetic only.
-//  * split_gemm_kernel: persistent, one CTA per SM, warp-specialised: warp 0
-//    streams tile pairs with 1-D TMA bulk copies (cp.async.bulk) into a
-//    6-stage mbarrier ring, warp 1 issues tcgen05.mma (M=128, N=128, K=16)
-//    into two TMEM accumulator slots, warps 2-9 drain the slots with
-//    tcgen05.ld and do the integer recombination and the FP64 epilogue.
-//    Small instances are packed along the diagonal of a 128 x 128 unit.
+//  * split_slice_kernel: one CTA per line block (128 rows of A, or BN columns
+//    of B): exponents, digit planes written as pre-swizzled BF16 tiles of 64 k
+//    (the exact SWIZZLE_128B K-major shared-memory image), the s planes of one
+//    k-block stored next to each other, per-line norm exponents. Integer
+//    arithmetic only.
+//  * split_gemm_kernel<BN>: persistent, one CTA per SM, warp-specialised.
+//    Output tile 128 x BN with BN = the largest multiple of 16 with
+//    s BN <= 512, so that the s level accumulators (one per t) all live in
+//    TMEM at once. Per k-block, warp 0 copies the s B planes with one 1-D TMA
+//    bulk copy (cp.async.bulk) and streams the s A planes through a ring of
+//    16 KiB slots; warp 1 issues, for each A plane p, one tcgen05.mma over the
+//    N-concatenation of B planes 1..s+1-p, which lands every product of the
+//    plane pair (p, q) in the accumulator of its level p + q -- one A tile
+//    and one B tile read per plane instead of per plane pair. Warps 2-9 drain
+//    each level as soon as its last MMA completes, do the integer
+//    recombination, free TMEM and then convert and store while the next tile
+//    is already being multiplied.
+//    Small instances are packed along the diagonal of a 128 x BN tile.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -56,15 +64,23 @@ namespace bg {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int kTileBytes = BM * BK * 2;  // 16 KiB, also BN x BK for B
-constexpr int kStages = 6;
+constexpr int BM = 128, BK = 64;
+constexpr int kATileBytes = BM * BK * 2;  // 16 KiB: one A plane of one k-block
+constexpr int kLineBytes = BK * 2;        // 128 bytes: one row of a tile
+constexpr int kMaxAStages = 8;
 constexpr int kGemmThreads = 320;
 constexpr int kEpiWarps = 8;
 constexpr int kMetaStride = 264;  // int32 per block: e[128], R[128], max R at [256]
-constexpr int kTmemCols = 256;    // two accumulator slots of BN columns
+constexpr int kTmemCols = 512;
 constexpr int kSliceThreads = 256;
+constexpr int kMaxDynSmem = 232448;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any single wait
+
+// Tile width (columns of the output tile, rows of a B tile) for s planes:
+// the largest multiple of 16 (at most 128) with s * BN <= 512 TMEM columns.
+__host__ __device__ constexpr int bn_for(int s) {
+  return s <= 4 ? 128 : s == 5 ? 96 : s == 6 ? 80 : s <= 8 ? 64 : s <= 10 ? 48 : 32;
+}
 
 struct SInst {
   int64_t a_off, b_off, c_off;  // user element offsets
@@ -74,7 +90,7 @@ struct SInst {
 };
 
 struct SliceJob {
-  int64_t tile0;  // first tile (plane 1, k-block 0) of the block
+  int64_t tile0;  // first tile of the block (k-block 0, plane 1)
   int32_t blk;    // block id = meta index
   int32_t pos;    // first position in the order list
   int16_t side;   // 0: A block (rows), 1: B block (columns)
@@ -86,20 +102,16 @@ struct SliceJob {
 };
 
 struct SplitUnit {
-  int64_t a_tile0, b_tile0;  // first tiles (chain mode: a_tile0 = row-block offset in tiles)
-  int32_t a_blk, b_blk;      // meta blocks (chain mode: a_blk = row block index)
+  int64_t a_tile0, b_tile0;  // first tiles (chain mode: a_tile0 is relative to the pool entry)
+  int32_t a_blk, b_blk;      // meta blocks (chain mode: a_blk is the row block index)
   int32_t pos;               // order position of the (first) instance
   int16_t g;                 // packed instances (1 = a tile of one instance)
   int16_t nkb;               // k-blocks
-  int16_t kmma_last;         // MMAs (K = 16) in the last k-block
+  int16_t kmma_last;         // MMA K-steps (16 each) in the last k-block
   int16_t mrow;              // virtual rows per packed instance
   int16_t ncol;              // columns per packed instance
   int16_t pad;
   int32_t r0, c0;            // tile origin in the instance (virtual rows, columns)
-};
-
-struct LevelTable {
-  int8_t kcb[kMaxSlices + 3];  // chunk size in k-blocks for level t (index t)
 };
 
 struct SliceArgs {
@@ -115,7 +127,7 @@ struct SliceArgs {
   uint8_t* tilesB;
   int32_t* metaA;
   int32_t* metaB;
-  int cplx, s, beta;
+  int cplx, s, beta, bn;
 };
 
 struct GemmArgs {
@@ -135,7 +147,8 @@ struct GemmArgs {
   int32_t pool_count;         // chain mode: number of pool entries
   Scalars sc;
   int cplx, s, beta, skip_product;
-  LevelTable lv;
+  int kpass;                  // k-blocks per exact pass
+  int a_stages;               // slots of the A ring
   int* err;
 };
 
@@ -259,17 +272,11 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
+        "=r"(r[7])
       : "r"(taddr));
 }
 
@@ -293,6 +300,8 @@ __device__ __forceinline__ int line_exponent(unsigned long long maxbits) {
 // the balancing bias sum_{p=1..S} half 2^(beta (S-p)) and 2^-beta.
 struct DigitCtx {
   int beta, half, mask;
+  bool narrow;  // S beta <= 60: the fixed-point value fits 64-bit arithmetic
+  long long bias64;
   __int128 bias;
   float step;
 };
@@ -303,9 +312,11 @@ __device__ __forceinline__ DigitCtx digit_ctx(int beta) {
   c.beta = beta;
   c.half = 1 << (beta - 1);
   c.mask = (1 << beta) - 1;
+  c.narrow = S * beta <= 60;
   c.bias = 0;
 #pragma unroll
   for (int p = 0; p < S; ++p) c.bias = (c.bias << beta) + c.half;
+  c.bias64 = (long long)c.bias;
   c.step = __int_as_float((127 - beta) << 23);
   return c;
 }
@@ -329,21 +340,34 @@ __device__ __forceinline__ float make_digits(double x, int e, const DigitCtx& c,
     q = eb - 1075;
   }
   const int sh = q - e + S * c.beta;
-  unsigned __int128 N = 0;
-  if (M != 0) {
-    if (sh >= 0) {
-      N = (unsigned __int128)M << sh;
-    } else if (sh > -64) {
-      N = (unsigned __int128)((M + (1ull << (-sh - 1))) >> (-sh));
+  const bool neg = (bits >> 63) != 0;
+  if (c.narrow) {
+    unsigned long long N = 0;
+    if (M != 0) {
+      if (sh >= 0) N = M << sh;
+      else if (sh > -64) N = (M + (1ull << (-sh - 1))) >> (-sh);
     }
-  }
-  __int128 Np = ((bits >> 63) ? -(__int128)N : (__int128)N) + c.bias;
+    long long Np = (neg ? -(long long)N : (long long)N) + c.bias64;
 #pragma unroll
-  for (int p = S - 1; p >= 1; --p) {
-    d[p] = (int)((long long)Np & c.mask) - c.half;
-    Np >>= c.beta;
+    for (int p = S - 1; p >= 1; --p) {
+      d[p] = (int)(Np & c.mask) - c.half;
+      Np >>= c.beta;
+    }
+    d[0] = (int)Np - c.half;
+  } else {
+    unsigned __int128 N = 0;
+    if (M != 0) {
+      if (sh >= 0) N = (unsigned __int128)M << sh;
+      else if (sh > -64) N = (unsigned __int128)((M + (1ull << (-sh - 1))) >> (-sh));
+    }
+    __int128 Np = (neg ? -(__int128)N : (__int128)N) + c.bias;
+#pragma unroll
+    for (int p = S - 1; p >= 1; --p) {
+      d[p] = (int)((long long)Np & c.mask) - c.half;
+      Np >>= c.beta;
+    }
+    d[0] = (int)(long long)Np - c.half;
   }
-  d[0] = (int)(long long)Np - c.half;
   float alpha = 0.f, w = 1.f;
 #pragma unroll
   for (int p = 0; p < S; ++p) {
@@ -386,6 +410,9 @@ __device__ __forceinline__ double valB(const double* B, const SInst& in, int cpl
 
 // ---- slicer ----------------------------------------------------------------------------------
 
+// Tile layout (A and B alike): the tile of plane p (0-based) and k-block kb
+// of a block is tile number tile0 + kb * S + p; tiles are `lines` rows of 128
+// bytes (64 BF16 values of k), chunk c of row r stored at chunk c ^ (r & 7).
 template <int S>
 __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceArgs a) {
   const DigitCtx dc = digit_ctx<S>(a.beta);
@@ -398,6 +425,9 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
     const SliceJob J = a.jobs[jb];
     const bool isA = J.side == 0;
     const int kv = J.kv;
+    const int lines = isA ? BM : a.bn;
+    const int tile_bytes = lines * kLineBytes;
+    uint8_t* tiles = isA ? a.tilesA : a.tilesB;
     // ---- phase 1: line maxima
     if (isA) {
       const int l = t & 127, h = t >> 7;
@@ -420,7 +450,7 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
       for (int l = warp * 16; l < warp * 16 + 16; ++l) {
         const int li = l / J.span;
         unsigned long long mx = 0;
-        if (li < J.g) {
+        if (l < lines && li < J.g) {
           const SInst in = a.instB[a.orderB[J.pos + li]];
           const int c = J.org + l % J.span;
           if (c < in.n)
@@ -478,15 +508,16 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
             const float al1 = make_digits<S>(x1, e, dc, d1);
             n2 = fmaf(al0, al0, n2);
             n2 = fmaf(al1, al1, n2);
-            #pragma unroll
-            for (int p = 0; p < S; ++p) w[p][u >> 1] = bf16_of_int(d[p]) | (bf16_of_int(d1[p]) << 16);
-          }
-          const int64_t rowoff = (int64_t)l * 128 + ((cc ^ (l & 7)) << 4);
 #pragma unroll
-          for (int p = 0; p < S; ++p) {
-            uint8_t* dst = a.tilesA + (J.tile0 + (int64_t)p * J.nkb + kb) * kTileBytes + rowoff;
-            *reinterpret_cast<uint4*>(dst) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+            for (int p = 0; p < S; ++p)
+              w[p][u >> 1] = bf16_of_int(d[p]) | (bf16_of_int(d1[p]) << 16);
           }
+          uint8_t* dst = tiles + (J.tile0 + (int64_t)kb * S) * tile_bytes + l * kLineBytes +
+                         ((cc ^ (l & 7)) << 4);
+#pragma unroll
+          for (int p = 0; p < S; ++p)
+            *reinterpret_cast<uint4*>(dst + (int64_t)p * tile_bytes) =
+                make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
         }
       }
       s_n2[h][l] = n2;
@@ -494,13 +525,14 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
       float n2[4] = {0.f, 0.f, 0.f, 0.f};
       const int cc = lane & 7;
       for (int kb = 0; kb < J.nkb; ++kb) {
+#pragma unroll
         for (int it = 0; it < 4; ++it) {
           const int l = it * 32 + warp * 4 + (lane >> 3);
           const int li = l / J.span;
           bool cvalid = false;
           SInst in{};
           int c = 0;
-          if (li < J.g) {
+          if (l < lines && li < J.g) {
             in = a.instB[a.orderB[J.pos + li]];
             c = J.org + l % J.span;
             cvalid = c < in.n;
@@ -517,17 +549,21 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
             const float al1 = make_digits<S>(x1, e, dc, d1);
             n2[it] = fmaf(al0, al0, n2[it]);
             n2[it] = fmaf(al1, al1, n2[it]);
-            #pragma unroll
-            for (int p = 0; p < S; ++p) w[p][u >> 1] = bf16_of_int(d[p]) | (bf16_of_int(d1[p]) << 16);
-          }
-          const int64_t rowoff = (int64_t)l * 128 + ((cc ^ (l & 7)) << 4);
 #pragma unroll
-          for (int p = 0; p < S; ++p) {
-            uint8_t* dst = a.tilesB + (J.tile0 + (int64_t)p * J.nkb + kb) * kTileBytes + rowoff;
-            *reinterpret_cast<uint4*>(dst) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+            for (int p = 0; p < S; ++p)
+              w[p][u >> 1] = bf16_of_int(d[p]) | (bf16_of_int(d1[p]) << 16);
+          }
+          if (l < lines) {
+            uint8_t* dst = tiles + (J.tile0 + (int64_t)kb * S) * tile_bytes + l * kLineBytes +
+                           ((cc ^ (l & 7)) << 4);
+#pragma unroll
+            for (int p = 0; p < S; ++p)
+              *reinterpret_cast<uint4*>(dst + (int64_t)p * tile_bytes) =
+                  make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
           }
         }
       }
+#pragma unroll
       for (int it = 0; it < 4; ++it) {
         float v = n2[it];
         v += __shfl_xor_sync(0xFFFFFFFFu, v, 1);
@@ -544,7 +580,7 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
     // ---- phase 3: meta (exponent, norm exponent, block max of the norm exponent)
     int32_t* meta = (isA ? a.metaA : a.metaB) + (int64_t)J.blk * kMetaStride;
     if (t < 128) {
-      const int R = norm_exponent(s_n2[0][t] + s_n2[1][t]);
+      const int R = t < lines ? norm_exponent(s_n2[0][t] + s_n2[1][t]) : -126;
       s_R[t] = R;
       meta[t] = s_e[t];
       meta[128 + t] = R;
@@ -563,17 +599,17 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
 
 // ---- GEMM --------------------------------------------------------------------------------------
 
-struct GemmSmem {
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
-  uint64_t acc_full[2];
-  uint64_t acc_empty[2];
+struct GemmBars {
+  uint64_t b_full[2];
+  uint64_t b_empty[2];
+  uint64_t a_full[kMaxAStages];
+  uint64_t a_empty[kMaxAStages];
+  uint64_t lvl_full[kMaxSlices];
+  uint64_t tmem_free;
   uint64_t mma_done;
   uint32_t tmem_base;
   int abort_flag;
 };
-
-constexpr size_t kGemmSmemBytes = 1024 + 2 * kStages * kTileBytes + sizeof(GemmSmem);
 
 // Resolves the tiles and meta block of a unit. In chain mode the A side is
 // the pool matrix named by the walker's index for this step; an index out of
@@ -599,6 +635,14 @@ __device__ __forceinline__ bool unit_tiles(const GemmArgs& g, const SplitUnit& U
   return true;
 }
 
+__device__ __forceinline__ int unit_passes(const GemmArgs& g, const SplitUnit& U) {
+  if (g.skip_product || U.nkb <= 0) return 0;
+  return (U.nkb + g.kpass - 1) / g.kpass;
+}
+
+// Exactly rounded FP64 value of a * 2^E (a a 64-bit integer), by integer
+// operations (round to nearest even), with FP64 scaling only outside the
+// normal range.
 __device__ __forceinline__ double fixed_to_double(long long a, int E) {
   if (a == 0) return 0.0;
   const unsigned long long sign = a < 0 ? (1ull << 63) : 0ull;
@@ -621,26 +665,33 @@ __device__ __forceinline__ double fixed_to_double(long long a, int E) {
   return sign ? -v : v;
 }
 
+template <int BN>
 __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmArgs g) {
+  constexpr int COLS = BN / 2;  // output columns per epilogue thread
+  constexpr int BTILE = BN * kLineBytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
-  uint8_t* stA = smem;
-  uint8_t* stB = smem + kStages * kTileBytes;
-  GemmSmem& S = *reinterpret_cast<GemmSmem*>(smem + 2 * kStages * kTileBytes);
+  const int s = g.s;
+  const int bplanes_bytes = s * BTILE;
+  uint8_t* bbuf = smem;                          // 2 x s B tiles
+  uint8_t* aring = smem + 2 * bplanes_bytes;     // a_stages x 16 KiB
+  GemmBars& S = *reinterpret_cast<GemmBars*>(aring + g.a_stages * kATileBytes);
   volatile int* abort_flag = &S.abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = g.s;
+  const int NA = g.a_stages;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; ++i) {
-      mbar_init(&S.full[i], 1);
-      mbar_init(&S.empty[i], 1);
-    }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&S.acc_full[i], 1);
-      mbar_init(&S.acc_empty[i], kEpiWarps);
+      mbar_init(&S.b_full[i], 1);
+      mbar_init(&S.b_empty[i], 1);
     }
+    for (int i = 0; i < NA; ++i) {
+      mbar_init(&S.a_full[i], 1);
+      mbar_init(&S.a_empty[i], 1);
+    }
+    for (int i = 0; i < s; ++i) mbar_init(&S.lvl_full[i], 1);
+    mbar_init(&S.tmem_free, kEpiWarps);
     mbar_init(&S.mma_done, 1);
     S.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -657,98 +708,118 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
   const uint32_t tmem_base = S.tmem_base;
 
   if (warp == 0) {
-    // ---------------- producer: TMA bulk copies of tile pairs ----------------
+    // ---------------- producer: one TMA bulk copy of the s B planes per k-block, and
+    // the s A planes of the k-block through the A ring
     if (lane == 0) {
-      uint32_t it = 0;
+      uint32_t kbc = 0, afill = 0;
       bool ok = true;
-      for (int64_t u = blockIdx.x; u < g.nunits && ok && !g.skip_product; u += gridDim.x) {
+      for (int64_t u = blockIdx.x; u < g.nunits && ok; u += gridDim.x) {
         const SplitUnit U = g.units[u];
         int64_t at, bt;
         int ablk;
         if (!unit_tiles(g, U, &at, &bt, &ablk)) continue;
-        for (int t = 2; t <= s + 1 && ok; ++t) {
-          const int kc = g.lv.kcb[t];
-          for (int kb0 = 0; kb0 < U.nkb && ok; kb0 += kc) {
-            const int kb1 = min((int)U.nkb, kb0 + kc);
-            for (int p = 1; p < t && ok; ++p) {
-              const int q = t - p;
-              for (int kb = kb0; kb < kb1; ++kb) {
-                const int st = it % kStages;
-                const uint32_t use = it / kStages;
-                if (use > 0 && !mbar_wait(&S.empty[st], (use - 1) & 1, abort_flag)) {
-                  record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_EMPTY_BARRIER, (int)u);
-                  *abort_flag = 1;
-                  ok = false;
-                  break;
-                }
-                mbar_arrive_expect_tx(&S.full[st], 2 * kTileBytes);
-                bulk_g2s(stA + st * kTileBytes,
-                         g.tilesA + (at + (int64_t)(p - 1) * U.nkb + kb) * kTileBytes, kTileBytes,
-                         &S.full[st]);
-                bulk_g2s(stB + st * kTileBytes,
-                         g.tilesB + (bt + (int64_t)(q - 1) * U.nkb + kb) * kTileBytes, kTileBytes,
-                         &S.full[st]);
-                ++it;
+        const int npass = unit_passes(g, U);
+        for (int c = 0; c < npass && ok; ++c) {
+          const int kb_lo = c * g.kpass, kb_hi = min((int)U.nkb, kb_lo + g.kpass);
+          for (int kb = kb_lo; kb < kb_hi && ok; ++kb, ++kbc) {
+            const int buf = kbc & 1;
+            const uint32_t use = kbc >> 1;
+            if (use > 0 && !mbar_wait(&S.b_empty[buf], (use - 1) & 1, abort_flag)) {
+              record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_EMPTY_BARRIER, (int)u);
+              *abort_flag = 1;
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&S.b_full[buf], (uint32_t)bplanes_bytes);
+            bulk_g2s(bbuf + buf * bplanes_bytes, g.tilesB + (bt + (int64_t)kb * s) * BTILE,
+                     (uint32_t)bplanes_bytes, &S.b_full[buf]);
+            for (int p = 0; p < s; ++p, ++afill) {
+              const int slot = afill % NA;
+              const uint32_t ause = afill / NA;
+              if (ause > 0 && !mbar_wait(&S.a_empty[slot], (ause - 1) & 1, abort_flag)) {
+                record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_EMPTY_BARRIER, (int)u);
+                *abort_flag = 1;
+                ok = false;
+                break;
               }
+              mbar_arrive_expect_tx(&S.a_full[slot], kATileBytes);
+              bulk_g2s(aring + slot * kATileBytes,
+                       g.tilesA + (at + (int64_t)kb * s + p) * kATileBytes, kATileBytes,
+                       &S.a_full[slot]);
             }
           }
         }
       }
       // let every copy this thread started land before the CTA can exit
-      const uint32_t first = it > (uint32_t)kStages ? it - kStages : 0;
-      for (uint32_t j = first; j < it; ++j) mbar_wait_time(&S.full[j % kStages], (j / kStages) & 1);
+      for (uint32_t j = kbc > 2 ? kbc - 2 : 0; j < kbc; ++j)
+        mbar_wait_time(&S.b_full[j & 1], (j >> 1) & 1);
+      for (uint32_t j = afill > (uint32_t)NA ? afill - NA : 0; j < afill; ++j)
+        mbar_wait_time(&S.a_full[j % NA], (j / NA) & 1);
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
+    // ---------------- MMA issuer: one N-concatenated MMA per A plane and K-step
     if (lane == 0) {
-      constexpr uint32_t idesc = make_idesc(BM, BN);
-      uint32_t it = 0, drain = 0;
+      uint32_t kbc = 0, passc = 0;
+      int slot = 0;
+      uint32_t aphase = 0;
       bool ok = true;
-      for (int64_t u = blockIdx.x; u < g.nunits && ok && !g.skip_product; u += gridDim.x) {
+      const uint32_t bbase = smem_u32(bbuf);
+      const uint32_t abase = smem_u32(aring);
+      for (int64_t u = blockIdx.x; u < g.nunits && ok; u += gridDim.x) {
         const SplitUnit U = g.units[u];
         int64_t at_, bt_;
         int ablk_;
         if (!unit_tiles(g, U, &at_, &bt_, &ablk_)) continue;
-        for (int t = 2; t <= s + 1 && ok; ++t) {
-          const int kc = g.lv.kcb[t];
-          for (int kb0 = 0; kb0 < U.nkb && ok; kb0 += kc) {
-            const int kb1 = min((int)U.nkb, kb0 + kc);
-            const int slot = drain & 1;
-            const uint32_t suse = drain >> 1;
-            if (suse > 0 && !mbar_wait(&S.acc_empty[slot], (suse - 1) & 1, abort_flag)) {
-              record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_ACC_EMPTY, (int)u);
+        const int npass = unit_passes(g, U);
+        for (int c = 0; c < npass && ok; ++c, ++passc) {
+          if (passc > 0 && !mbar_wait(&S.tmem_free, (passc - 1) & 1, abort_flag)) {
+            record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_ACC_EMPTY, (int)u);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int kb_lo = c * g.kpass, kb_hi = min((int)U.nkb, kb_lo + g.kpass);
+          for (int kb = kb_lo; kb < kb_hi && ok; ++kb, ++kbc) {
+            const int buf = kbc & 1;
+            if (!mbar_wait(&S.b_full[buf], (kbc >> 1) & 1, abort_flag)) {
+              record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_FULL_BARRIER, (int)u);
               *abort_flag = 1;
               ok = false;
               break;
             }
-            tc_fence_after();
-            const uint32_t d_tmem = tmem_base + slot * BN;
-            uint32_t acc = 0;
-            for (int p = 1; p < t && ok; ++p) {
-              for (int kb = kb0; kb < kb1; ++kb) {
-                const int st = it % kStages;
-                const uint32_t use = it / kStages;
-                if (!mbar_wait(&S.full[st], use & 1, abort_flag)) {
-                  record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_FULL_BARRIER, (int)u);
-                  *abort_flag = 1;
-                  ok = false;
-                  break;
+            const uint64_t bdesc = sw128_desc(bbase + buf * bplanes_bytes);
+            const int nk = (kb == U.nkb - 1) ? U.kmma_last : 4;
+            const bool first_kb = kb == kb_lo, last_kb = kb == kb_hi - 1;
+            for (int p = 0; p < s; ++p) {
+              if (!mbar_wait(&S.a_full[slot], aphase, abort_flag)) {
+                record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_FULL_BARRIER, (int)u);
+                *abort_flag = 1;
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint64_t adesc = sw128_desc(abase + slot * kATileBytes);
+              const int ncat = (s - p) * BN;  // B planes 1..s-p: levels p+2 .. s+1
+              const uint32_t dcol = tmem_base + p * BN;
+              for (int kk = 0; kk < nk; ++kk) {
+                const uint32_t acc = (first_kb && kk == 0 && p == 0) ? 0u : 1u;
+                for (int n0 = 0; n0 < ncat; n0 += 256) {
+                  const int nn = min(256, ncat - n0);
+                  umma_bf16(dcol + n0, adesc + 2 * kk,
+                            bdesc + (uint64_t)((n0 * kLineBytes) >> 4) + 2 * kk,
+                            make_idesc(BM, nn), acc);
                 }
-                tc_fence_after();
-                const uint64_t ad = sw128_desc(smem_u32(stA + st * kTileBytes));
-                const uint64_t bd = sw128_desc(smem_u32(stB + st * kTileBytes));
-                const int nmma = (kb == U.nkb - 1) ? U.kmma_last : 4;
-                for (int kk = 0; kk < nmma; ++kk) {
-                  umma_bf16(d_tmem, ad + 2 * kk, bd + 2 * kk, idesc, acc);
-                  acc = 1;
-                }
-                umma_commit(&S.empty[st]);
-                ++it;
+              }
+              umma_commit(&S.a_empty[slot]);
+              if (last_kb) umma_commit(&S.lvl_full[p]);  // level p+2 is complete
+              if (++slot == NA) {
+                slot = 0;
+                aphase ^= 1;
               }
             }
             if (!ok) break;
-            umma_commit(&S.acc_full[slot]);
-            ++drain;
+            umma_commit(&S.b_empty[buf]);
           }
         }
       }
@@ -757,14 +828,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
       mbar_wait_time(&S.mma_done, 0);
     }
   } else {
-    // ---------------- epilogue: drain, recombine, store ----------------
-    const int ew = warp - 2;
+    // ---------------- epilogue: drain levels, recombine, free TMEM, store
     const int quad = warp & 3;
-    const int half = ew >> 2;
+    const int half = (warp - 2) >> 2;
     const int row = quad * 32 + lane;
-    const uint32_t tq = tmem_base + ((uint32_t)(quad * 32) << 16) + half * 64;
+    const int col0 = half * COLS;
+    const uint32_t tq = tmem_base + ((uint32_t)(quad * 32) << 16) + col0;
     const bool alpha_one = g.sc.alpha_re == 1.0 && g.sc.alpha_im == 0.0;
-    uint32_t drain = 0;
+    uint32_t passc = 0;
     bool ok = true;
     for (int64_t u = blockIdx.x; u < g.nunits && ok; u += gridDim.x) {
       const SplitUnit U = g.units[u];
@@ -779,21 +850,41 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
       const int32_t* mb = g.metaB + (int64_t)U.b_blk * kMetaStride;
       const int e_i = ma[row];
       const int F = ma[128 + row] + mb[256] + 1;
-      long long acc[64];
+      // output rows/columns of this thread
+      int rr, inst_pos, cmin, cmax, coff;
+      bool rvalid;
+      if (U.g > 1) {
+        const int li = row / U.mrow;
+        rr = row - li * U.mrow;
+        rvalid = li < U.g;
+        inst_pos = U.pos + (rvalid ? li : 0);
+        cmin = li * U.ncol;
+        cmax = cmin + U.ncol;
+        coff = -cmin;
+      } else {
+        rr = U.r0 + row;
+        inst_pos = U.pos;
+        rvalid = true;
+        cmin = 0;
+        cmax = BN;
+        coff = U.c0;
+      }
+      const SInst in = g.inst[g.order[inst_pos]];
+      const int mv = g.cplx ? 2 * in.m : in.m;
+      rvalid = rvalid && rr < mv;
+      if (U.g == 1) cmax = min(cmax, in.n - U.c0);
+      const int64_t cbase = (g.cplx ? 2 * in.c_off : in.c_off) + rr;
+      const int64_t ldcv = g.cplx ? 2 * in.ldc : in.ldc;
+      const int Ebase = F - 62 + e_i - 2 * g.beta;
+      const int npass = unit_passes(g, U);
+      for (int c = 0; c < max(npass, 1) && ok; ++c) {
+        long long acc[COLS];
 #pragma unroll
-      for (int j = 0; j < 64; ++j) acc[j] = 0;
-      if (!g.skip_product) {
-        for (int t = 2; t <= s + 1 && ok; ++t) {
-          const int kc = g.lv.kcb[t];
-          int sh = 62 - F - g.beta * (t - 2);
-          sh = max(-63, min(62, sh));
-          const int lsh = sh > 0 ? sh : 0, rsh = sh < 0 ? -sh : 0;
-          const long long rnd = rsh > 0 ? (1ll << (rsh - 1)) : 0ll;
-          for (int kb0 = 0; kb0 < U.nkb && ok; kb0 += kc) {
-            const int slot = drain & 1;
-            const uint32_t suse = drain >> 1;
+        for (int j = 0; j < COLS; ++j) acc[j] = 0;
+        if (npass > 0) {
+          for (int lv = 0; lv < s; ++lv) {
             bool got = true;
-            if (lane == 0) got = mbar_wait(&S.acc_full[slot], suse & 1, abort_flag);
+            if (lane == 0) got = mbar_wait(&S.lvl_full[lv], passc & 1, abort_flag);
             got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
             if (!got) {
               if (lane == 0) {
@@ -804,81 +895,70 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
               break;
             }
             tc_fence_after();
+            int sh = 62 - F - g.beta * lv;
+            sh = max(-63, min(62, sh));
+            const int lsh = sh > 0 ? sh : 0, rsh = sh < 0 ? -sh : 0;
+            const long long rnd = rsh > 0 ? (1ll << (rsh - 1)) : 0ll;
 #pragma unroll
-            for (int c2 = 0; c2 < 2; ++c2) {
-              uint32_t v[32];
-              tmem_ld32(tq + slot * BN + 32 * c2, v);
+            for (int j0 = 0; j0 < COLS; j0 += 16) {
+              uint32_t v0[8], v1[8];
+              tmem_ld8(tq + lv * BN + j0, v0);
+              if (j0 + 8 < COLS) tmem_ld8(tq + lv * BN + j0 + 8, v1);
               tmem_ld_wait();
-              if (c2 == 1) {
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&S.acc_empty[slot]);
-              }
 #pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const long long L = (long long)__float2int_rn(__uint_as_float(v[j]));
-                acc[32 * c2 + j] += ((L << lsh) + rnd) >> rsh;
+              for (int j = 0; j < 8; ++j) {
+                const long long L = (long long)__float2int_rn(__uint_as_float(v0[j]));
+                acc[j0 + j] += ((L << lsh) + rnd) >> rsh;
+              }
+              if (j0 + 8 < COLS) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  const long long L = (long long)__float2int_rn(__uint_as_float(v1[j]));
+                  acc[j0 + 8 + j] += ((L << lsh) + rnd) >> rsh;
+                }
               }
             }
-            ++drain;
           }
+          if (!ok) break;
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&S.tmem_free);
+          ++passc;
         }
-      }
-      if (!ok) break;
-      // ---- final: exact conversion, alpha/beta, store
-      const int g_count = U.g;
-      int li = 0, rr, inst_pos;
-      bool rvalid;
-      if (g_count > 1) {
-        li = row / U.mrow;
-        rr = row - li * U.mrow;
-        rvalid = li < g_count;
-        inst_pos = U.pos + (rvalid ? li : 0);
-      } else {
-        rr = U.r0 + row;
-        inst_pos = U.pos;
-        rvalid = true;
-      }
-      const SInst in = g.inst[g.order[inst_pos]];
-      const int mv = g.cplx ? 2 * in.m : in.m;
-      rvalid = rvalid && rr < mv;
-      const int64_t cbase = (g.cplx ? 2 * in.c_off : in.c_off) + rr;
-      const int64_t ldcv = g.cplx ? 2 * in.ldc : in.ldc;
-      const int Ebase = F - 62 + e_i - 2 * g.beta;
+        // ---- exact conversion, alpha/beta, store (TMEM already free: overlaps the next MMAs)
+        const bool first_pass = c == 0;
+        for (int j0 = 0; j0 < COLS; j0 += 8) {
 #pragma unroll
-      for (int j = 0; j < 64; ++j) {
-        const int col = half * 64 + j;
-        int cc;
-        bool valid;
-        if (g_count > 1) {
-          const int lj = col / U.ncol;
-          cc = col - lj * U.ncol;
-          valid = rvalid && lj == li;
-        } else {
-          cc = U.c0 + col;
-          valid = rvalid && cc < in.n;
-        }
-        const int f_j = mb[col];
-        double x = valid ? fixed_to_double(acc[j], Ebase + f_j) : 0.0;
-        double* cp = g.C + cbase + (int64_t)cc * ldcv;
-        if (!g.cplx) {
-          if (valid) {
-            double v = alpha_one ? x : g.sc.alpha_re * x;
-            if (g.skip_product) v = 0.0;
-            if (!g.sc.beta_zero) v = fma(g.sc.beta_re, *cp, v);
-            *cp = v;
+          for (int j = 0; j < 8; ++j) {
+            const int col = col0 + j0 + j;
+            const bool valid = rvalid && col >= cmin && col < cmax;
+            const int cc = col + coff;
+            const double x = valid ? fixed_to_double(acc[j], Ebase + mb[col]) : 0.0;
+            double* cp = g.C + cbase + (int64_t)cc * ldcv;
+            if (!g.cplx) {
+              if (valid) {
+                double v = alpha_one ? x : g.sc.alpha_re * x;
+                if (!first_pass) v += *cp;
+                else if (!g.sc.beta_zero) v = fma(g.sc.beta_re, *cp, v);
+                *cp = v;
+              }
+            } else {
+              const double xp = __shfl_xor_sync(0xFFFFFFFFu, x, 1);
+              const bool need_c = valid && (!first_pass || !g.sc.beta_zero);
+              const double cv = need_c ? *cp : 0.0;
+              const double cpn = __shfl_xor_sync(0xFFFFFFFFu, cv, 1);
+              if (valid) {
+                const double sgn = (rr & 1) ? 1.0 : -1.0;  // im row: +, re row: -
+                double v = fma(g.sc.alpha_re, x, sgn * g.sc.alpha_im * xp);
+                if (!first_pass) v += cv;
+                else if (!g.sc.beta_zero) v = fma(g.sc.beta_re, cv, fma(sgn * g.sc.beta_im, cpn, v));
+                *cp = v;
+              }
+            }
           }
-        } else {
-          const double xp = __shfl_xor_sync(0xFFFFFFFFu, x, 1);
-          const double c = (valid && !g.sc.beta_zero) ? *cp : 0.0;
-          const double cpn = __shfl_xor_sync(0xFFFFFFFFu, c, 1);
-          if (valid) {
-            const double sgn = (rr & 1) ? 1.0 : -1.0;  // im row: +, re row: -
-            double v = g.skip_product ? 0.0
-                                      : fma(g.sc.alpha_re, x, sgn * g.sc.alpha_im * xp);
-            if (!g.sc.beta_zero) v = fma(g.sc.beta_re, c, fma(sgn * g.sc.beta_im, cpn, v));
-            *cp = v;
-          }
+          // rotate the next 8 accumulators into place (keeps the loop body small)
+#pragma unroll
+          for (int j = 0; j + 8 < COLS; ++j) acc[j] = acc[j + 8];
         }
       }
     }
@@ -904,7 +984,8 @@ __global__ void planes_exp_kernel(int64_t m, int64_t k, const double* X, int64_t
     unsigned long long mx = 0;
     for (int64_t i = 0; i < len; ++i) {
       const double x = axis == 0 ? X[l + i * ldx] : X[i + l * ldx];
-      const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+      const unsigned long long b =
+          (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
       mx = b > mx ? b : mx;
     }
     exps[l] = line_exponent(mx);
@@ -926,9 +1007,10 @@ __global__ void planes_digit_kernel(int64_t m, int64_t k, const double* X, int64
   }
 }
 
-// Expands BODY once per slice count S = 1..12 and runs the one matching `s`.
-#define BG_DISPATCH_SLICES(s, ...)               \
-  switch (s) {                                   \
+// Expands the variadic body once per slice count S = 1..12 and runs the one
+// matching `s`.
+#define BG_DISPATCH_SLICES(s, ...)                      \
+  switch (s) {                                          \
     case 1: { constexpr int S = 1; __VA_ARGS__; }       \
     case 2: { constexpr int S = 2; __VA_ARGS__; }       \
     case 3: { constexpr int S = 3; __VA_ARGS__; }       \
@@ -941,7 +1023,19 @@ __global__ void planes_digit_kernel(int64_t m, int64_t k, const double* X, int64
     case 10: { constexpr int S = 10; __VA_ARGS__; }     \
     case 11: { constexpr int S = 11; __VA_ARGS__; }     \
     case 12: { constexpr int S = 12; __VA_ARGS__; }     \
-    default: return cudaErrorInvalidValue;       \
+    default: return cudaErrorInvalidValue;              \
+  }
+
+// Same for the tile width BN (the GEMM kernel template argument).
+#define BG_DISPATCH_BN(bn, ...)                         \
+  switch (bn) {                                         \
+    case 128: { constexpr int BNV = 128; __VA_ARGS__; } \
+    case 96: { constexpr int BNV = 96; __VA_ARGS__; }   \
+    case 80: { constexpr int BNV = 80; __VA_ARGS__; }   \
+    case 64: { constexpr int BNV = 64; __VA_ARGS__; }   \
+    case 48: { constexpr int BNV = 48; __VA_ARGS__; }   \
+    case 32: { constexpr int BNV = 32; __VA_ARGS__; }   \
+    default: return cudaErrorInvalidValue;              \
   }
 
 }  // namespace
@@ -965,12 +1059,14 @@ cudaError_t launch_split_planes(int64_t m, int64_t k, const double* X, int64_t l
 
 // ---- host: plans ------------------------------------------------------------------------------
 
-int split_default_beta(int slices) { return slices <= 6 ? 8 : 7; }
+int split_default_beta(int slices) { return slices <= 6 ? 7 : 6; }
 
-// Largest number of 64-wide k-blocks per FP32 accumulation for level t such
-// that every partial sum of digit products stays below 2^24 (exact in FP32).
-static bool level_chunks(int s, int beta, LevelTable* lv) {
-  memset(lv, 0, sizeof *lv);
+// K-blocks of 64 per pass such that every partial sum of a level's digit
+// products stays below 2^24 (exact in FP32): with |d_1| <= 2^beta and
+// |d_p| <= 2^(beta-1) for p >= 2, the level-t sum of |d_p d_q| per k is at
+// most bound_t; the pass length is set by the largest bound. 0 = impossible.
+static int level_pass(int s, int beta) {
+  double worst = 0;
   for (int t = 2; t <= s + 1; ++t) {
     double bound = 0;
     for (int p = 1; p < t; ++p) {
@@ -979,23 +1075,22 @@ static bool level_chunks(int s, int beta, LevelTable* lv) {
       const double bq = q == 1 ? std::ldexp(1.0, beta) : std::ldexp(1.0, beta - 1);
       bound += bp * bq;
     }
-    const double kc = std::floor(16777216.0 / (bound * BK));
-    if (kc < 1) return false;
-    lv->kcb[t] = (int8_t)std::min(kc, 100.0);
+    worst = std::max(worst, bound);
   }
-  return true;
+  const double kc = std::floor(16777216.0 / (worst * BK));
+  return (int)std::min(kc, 4096.0);
 }
 
 struct SplitPlan {
   bg_dtype dt = BG_R64;
-  int s = 0, beta = 0;
-  LevelTable lv{};
+  int s = 0, beta = 0, bn = 0, kpass = 0, a_stages = 0;
+  size_t smem = 0;
   bool chain = false;
   int sms = 0;
   int64_t count = 0;
   // device
   SliceJob* d_jobs = nullptr;
-  int64_t n_jobs = 0, n_jobs_A = 0;  // A jobs first
+  int64_t n_jobs = 0, n_jobs_A = 0;  // A jobs first (chain plans)
   SplitUnit* d_units = nullptr;
   int64_t n_units = 0;
   SInst* d_inst = nullptr;       // instances (chain: walkers)
@@ -1011,8 +1106,7 @@ struct SplitPlan {
   int32_t* metaB = nullptr;
   int64_t bytes = 0;
   int grid_slice = 0, grid_gemm = 0;
-  // fixed-plan key
-  std::vector<int64_t> key;
+  std::vector<int64_t> key;  // fixed-size plan cache key
   std::string desc;
 };
 
@@ -1072,11 +1166,21 @@ static bool setup_common(SplitPlan* p, bg_dtype dt, const bg_precision& pr, int 
   p->dt = dt;
   p->s = pr.slices;
   p->beta = pr.beta_bits ? pr.beta_bits : split_default_beta(pr.slices);
+  p->bn = bn_for(p->s);
   p->sms = sms;
-  if (!level_chunks(p->s, p->beta, &p->lv)) {
+  p->kpass = level_pass(p->s, p->beta);
+  if (p->kpass < 1) {
     *err = "split mode: digit width too large for exact FP32 sums";
     return false;
   }
+  const size_t bbytes = 2 * (size_t)p->s * p->bn * kLineBytes;
+  const size_t budget = kMaxDynSmem - 1024 - sizeof(GemmBars);
+  p->a_stages = (int)std::min<size_t>(kMaxAStages, (budget - bbytes) / kATileBytes);
+  if (p->a_stages < 2) {
+    *err = "split mode: shared memory too small for this slice count";
+    return false;
+  }
+  p->smem = 1024 + bbytes + (size_t)p->a_stages * kATileBytes + sizeof(GemmBars);
   return true;
 }
 
@@ -1090,7 +1194,7 @@ static int kmma_last_of(int kv) {
 static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& table,
                                  std::string* err) {
   const bool cplx = p->dt == BG_C128;
-  const int s = p->s;
+  const int s = p->s, BN = p->bn;
   std::vector<SInst> inst(table.size());
   for (size_t i = 0; i < table.size(); ++i) {
     const bg_instance& t = table[i];
@@ -1114,15 +1218,18 @@ static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& t
     const int64_t mv = cplx ? 2 * m : m, kvv = cplx ? 2 * k : k;
     const int nkb = (int)((kvv + BK - 1) / BK);
     const auto& ids = kv.second;
-    const bool pack = mv <= 64 && n <= 64;
-    if (pack) {
-      const int gmax = (int)std::min<int64_t>(BM / mv, BN / n);
+    const int gmax = (int)std::min<int64_t>(BM / mv, BN / n);
+    if (gmax >= 2) {
       for (size_t s0 = 0; s0 < ids.size(); s0 += gmax) {
         const int gc = (int)std::min<size_t>(gmax, ids.size() - s0);
         const int32_t pos = (int32_t)order.size();
         for (int i = 0; i < gc; ++i) order.push_back(ids[s0 + i]);
-        SliceJob ja{tileA, blkA, pos, 0, (int16_t)gc, (int16_t)mv, (int16_t)nkb, 0, (int32_t)kvv};
-        SliceJob jb{tileB, blkB, pos, 1, (int16_t)gc, (int16_t)n, (int16_t)nkb, 0, (int32_t)kvv};
+        if (nkb > 0) {
+          jobsA.push_back(SliceJob{tileA, blkA, pos, 0, (int16_t)gc, (int16_t)mv, (int16_t)nkb, 0,
+                                   (int32_t)kvv});
+          jobsB.push_back(SliceJob{tileB, blkB, pos, 1, (int16_t)gc, (int16_t)n, (int16_t)nkb, 0,
+                                   (int32_t)kvv});
+        }
         SplitUnit U{};
         U.a_tile0 = tileA;
         U.b_tile0 = tileB;
@@ -1134,11 +1241,6 @@ static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& t
         U.kmma_last = (int16_t)kmma_last_of((int)kvv);
         U.mrow = (int16_t)mv;
         U.ncol = (int16_t)n;
-        U.r0 = U.c0 = 0;
-        if (nkb > 0) {
-          jobsA.push_back(ja);
-          jobsB.push_back(jb);
-        }
         units.push_back(U);
         tileA += (int64_t)s * nkb;
         tileB += (int64_t)s * nkb;
@@ -1166,6 +1268,7 @@ static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& t
           tileB += (int64_t)s * nkb;
           ++blkB;
         }
+        // row blocks inner: the units sharing a B block run side by side (L2 reuse)
         for (int64_t cb = 0; cb < cbs; ++cb)
           for (int64_t rb = 0; rb < rbs; ++rb) {
             SplitUnit U{};
@@ -1194,7 +1297,6 @@ static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& t
   std::stable_sort(jobsB.begin(), jobsB.end(),
                    [](const SliceJob& a, const SliceJob& b) { return a.nkb > b.nkb; });
   std::vector<SliceJob> jobs;
-  // interleave A and B jobs so both sides progress together
   size_t ia = 0, ib = 0;
   while (ia < jobsA.size() || ib < jobsB.size()) {
     if (ia < jobsA.size()) jobs.push_back(jobsA[ia++]);
@@ -1204,14 +1306,15 @@ static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& t
   p->n_jobs_A = (int64_t)jobsA.size();
   p->n_units = (int64_t)units.size();
   p->count = (int64_t)table.size();
+  const size_t btile = (size_t)BN * kLineBytes;
   cudaError_t e;
   if ((e = dput(&p->d_jobs, jobs, &p->bytes)) != cudaSuccess ||
       (e = dput(&p->d_units, units, &p->bytes)) != cudaSuccess ||
       (e = dput(&p->d_inst, inst, &p->bytes)) != cudaSuccess ||
       (e = dput(&p->d_order, order, &p->bytes)) != cudaSuccess ||
-      (e = dalloc(reinterpret_cast<void**>(&p->tilesA), (size_t)tileA * kTileBytes, &p->bytes)) !=
+      (e = dalloc(reinterpret_cast<void**>(&p->tilesA), (size_t)tileA * kATileBytes, &p->bytes)) !=
           cudaSuccess ||
-      (e = dalloc(reinterpret_cast<void**>(&p->tilesB), (size_t)tileB * kTileBytes, &p->bytes)) !=
+      (e = dalloc(reinterpret_cast<void**>(&p->tilesB), (size_t)tileB * btile, &p->bytes)) !=
           cudaSuccess ||
       (e = dalloc(reinterpret_cast<void**>(&p->metaA), (size_t)std::max(blkA, 1) * kMetaStride * 4,
                   &p->bytes)) != cudaSuccess ||
@@ -1227,24 +1330,29 @@ static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& t
 
 static void finish_desc(SplitPlan* p) {
   char buf[512];
-  std::string kc;
-  for (int t = 2; t <= p->s + 1; ++t) kc += (t > 2 ? "," : "") + std::to_string(p->lv.kcb[t]);
   snprintf(buf, sizeof buf,
-           "{\"slices\": %d, \"beta_bits\": %d, \"pairs\": %d, \"level_chunk_kblocks\": [%s], "
-           "\"units\": %lld, \"slice_jobs\": %lld, \"tile\": [%d, %d, %d], \"stages\": %d, "
-           "\"workspace_bytes\": %lld}",
-           p->s, p->beta, p->s * (p->s + 1) / 2, kc.c_str(), (long long)p->n_units,
-           (long long)p->n_jobs, BM, BN, BK, kStages, (long long)p->bytes);
+           "{\"slices\": %d, \"beta_bits\": %d, \"pairs\": %d, \"tile\": [%d, %d, %d], "
+           "\"kpass_kblocks\": %d, \"a_stages\": %d, \"smem_bytes\": %zu, \"units\": %lld, "
+           "\"slice_jobs\": %lld, \"workspace_bytes\": %lld}",
+           p->s, p->beta, p->s * (p->s + 1) / 2, BM, p->bn, BK, p->kpass, p->a_stages, p->smem,
+           (long long)p->n_units, (long long)p->n_jobs, (long long)p->bytes);
   p->desc = buf;
 }
 
+static cudaError_t set_gemm_attr(int bn) {
+  static bool done[6] = {false, false, false, false, false, false};
+  const int slot = bn == 128 ? 0 : bn == 96 ? 1 : bn == 80 ? 2 : bn == 64 ? 3 : bn == 48 ? 4 : 5;
+  if (done[slot]) return cudaSuccess;
+  BG_DISPATCH_BN(bn, {
+    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<BNV>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e == cudaSuccess) done[slot] = true;
+    return e;
+  });
+}
+
 static void grids(SplitPlan* p) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kGemmSmemBytes);
-    attr_set = true;
-  }
+  set_gemm_attr(p->bn);
   p->grid_gemm = (int)std::max<int64_t>(1, std::min<int64_t>(p->sms, p->n_units));
   int bps = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, split_slice_kernel<9>, kSliceThreads, 0);
@@ -1295,6 +1403,7 @@ static cudaError_t launch_slicer(SplitPlan* p, const SliceJob* jobs, int64_t njo
   a.cplx = p->dt == BG_C128;
   a.s = p->s;
   a.beta = p->beta;
+  a.bn = p->bn;
   const int grid = (int)std::min<int64_t>(p->grid_slice, njobs);
   BG_DISPATCH_SLICES(p->s, {
     split_slice_kernel<S><<<grid, kSliceThreads, 0, st>>>(a);
@@ -1326,11 +1435,14 @@ static cudaError_t launch_gemm(SplitPlan* p, void* C, const Scalars& sc, const i
   g.s = p->s;
   g.beta = p->beta;
   g.skip_product = sc.alpha_zero;
-  g.lv = p->lv;
+  g.kpass = p->kpass;
+  g.a_stages = p->a_stages;
   g.err = d_err;
-  split_gemm_kernel<<<p->grid_gemm, kGemmThreads, kGemmSmemBytes, st>>>(g);
-  count_launch();
-  return cudaGetLastError();
+  BG_DISPATCH_BN(p->bn, {
+    split_gemm_kernel<BNV><<<p->grid_gemm, kGemmThreads, p->smem, st>>>(g);
+    count_launch();
+    return cudaGetLastError();
+  });
 }
 
 bg_status split_plan_run(SplitPlan* p, const void* A, const void* B, void* C, const Scalars& s,
@@ -1401,7 +1513,7 @@ bg_status split_chain_create(SplitPlan** out, bg_dtype dt, const bg_precision& p
   }
   p->chain = true;
   const bool cplx = dt == BG_C128;
-  const int s = p->s;
+  const int s = p->s, BN = p->bn;
   // pool entries: A blocks (row blocks), sliced once per chain_step call
   std::vector<SInst> pool(pool_n.size());
   std::vector<int32_t> pool_order(pool_n.size());
@@ -1478,6 +1590,7 @@ bg_status split_chain_create(SplitPlan** out, bg_dtype dt, const bg_precision& p
   p->n_units = (int64_t)units.size();
   p->count = (int64_t)wn.size();
   p->n_pool = (int32_t)pool_n.size();
+  const size_t btile = (size_t)BN * kLineBytes;
   cudaError_t e;
   if ((e = dput(&p->d_jobs, jobs, &p->bytes)) != cudaSuccess ||
       (e = dput(&p->d_units, units, &p->bytes)) != cudaSuccess ||
@@ -1487,9 +1600,9 @@ bg_status split_chain_create(SplitPlan** out, bg_dtype dt, const bg_precision& p
       (e = dput(&p->d_pool_order, pool_order, &p->bytes)) != cudaSuccess ||
       (e = dput(&p->d_pool_tile0, pool_tile0, &p->bytes)) != cudaSuccess ||
       (e = dput(&p->d_pool_blk0, pool_blk0, &p->bytes)) != cudaSuccess ||
-      (e = dalloc(reinterpret_cast<void**>(&p->tilesA), (size_t)tileA * kTileBytes, &p->bytes)) !=
+      (e = dalloc(reinterpret_cast<void**>(&p->tilesA), (size_t)tileA * kATileBytes, &p->bytes)) !=
           cudaSuccess ||
-      (e = dalloc(reinterpret_cast<void**>(&p->tilesB), (size_t)tileB * kTileBytes, &p->bytes)) !=
+      (e = dalloc(reinterpret_cast<void**>(&p->tilesB), (size_t)tileB * btile, &p->bytes)) !=
           cudaSuccess ||
       (e = dalloc(reinterpret_cast<void**>(&p->metaA), (size_t)std::max(blkA, 1) * kMetaStride * 4,
                   &p->bytes)) != cudaSuccess ||

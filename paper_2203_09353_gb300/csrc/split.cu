@@ -665,14 +665,16 @@ __device__ __forceinline__ double fixed_to_double(long long a, int E) {
   return sign ? -v : v;
 }
 
-template <int BN>
+// SF > 0: the slice count is the compile-time constant SF (the MMA issue loop
+// unrolls completely); SF == 0: any slice count g.s with this tile width.
+template <int BN, int SF>
 __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmArgs g) {
   constexpr int COLS = BN / 2;  // output columns per epilogue thread
   constexpr int BTILE = BN * kLineBytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
-  const int s = g.s;
+  const int s = SF > 0 ? SF : g.s;
   const int bplanes_bytes = s * BTILE;
   uint8_t* bbuf = smem;                          // 2 x s B tiles
   uint8_t* aring = smem + 2 * bplanes_bytes;     // a_stages x 16 KiB
@@ -790,8 +792,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
             }
             const uint64_t bdesc = sw128_desc(bbase + buf * bplanes_bytes);
             const int nk = (kb == U.nkb - 1) ? U.kmma_last : 4;
-            const bool first_kb = kb == kb_lo, last_kb = kb == kb_hi - 1;
-            for (int p = 0; p < s; ++p) {
+            const bool last_kb = kb == kb_hi - 1;
+            uint32_t acc0 = kb == kb_lo ? 0u : 1u;  // the first MMA of a pass initialises TMEM
+#pragma unroll
+            for (int p = 0; p < (SF > 0 ? SF : kMaxSlices); ++p) {
+              if (SF == 0 && p >= s) break;
               if (!mbar_wait(&S.a_full[slot], aphase, abort_flag)) {
                 record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_FULL_BARRIER, (int)u);
                 *abort_flag = 1;
@@ -800,17 +805,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
               }
               tc_fence_after();
               const uint64_t adesc = sw128_desc(abase + slot * kATileBytes);
-              const int ncat = (s - p) * BN;  // B planes 1..s-p: levels p+2 .. s+1
-              const uint32_t dcol = tmem_base + p * BN;
-              for (int kk = 0; kk < nk; ++kk) {
-                const uint32_t acc = (first_kb && kk == 0 && p == 0) ? 0u : 1u;
-                for (int n0 = 0; n0 < ncat; n0 += 256) {
-                  const int nn = min(256, ncat - n0);
-                  umma_bf16(dcol + n0, adesc + 2 * kk,
-                            bdesc + (uint64_t)((n0 * kLineBytes) >> 4) + 2 * kk,
-                            make_idesc(BM, nn), acc);
+              // B planes 1..s-p (levels p+2 .. s+1) as one N range, cut in pieces of <= 256
+              const int ncat = (s - p) * BN;
+              const int n1 = ncat > 256 ? ncat - 256 : 0;
+              const uint32_t id0 = make_idesc(BM, ncat > 256 ? 256 : ncat);
+              const uint32_t id1 = make_idesc(BM, n1 > 0 ? n1 : 16);
+              const uint32_t d0 = tmem_base + p * BN;
+              constexpr uint64_t kB256 = (256 * kLineBytes) >> 4;
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                if (kk < nk) {
+                  const uint32_t acc = kk == 0 ? acc0 : 1u;
+                  umma_bf16(d0, adesc + 2 * kk, bdesc + 2 * kk, id0, acc);
+                  if (n1 > 0) umma_bf16(d0 + 256, adesc + 2 * kk, bdesc + kB256 + 2 * kk, id1, acc);
                 }
               }
+              acc0 = 1u;
               umma_commit(&S.a_empty[slot]);
               if (last_kb) umma_commit(&S.lvl_full[p]);  // level p+2 is complete
               if (++slot == NA) {
@@ -882,6 +892,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
 #pragma unroll
         for (int j = 0; j < COLS; ++j) acc[j] = 0;
         if (npass > 0) {
+#pragma unroll 1
           for (int lv = 0; lv < s; ++lv) {
             bool got = true;
             if (lane == 0) got = mbar_wait(&S.lvl_full[lv], passc & 1, abort_flag);
@@ -1026,16 +1037,19 @@ __global__ void planes_digit_kernel(int64_t m, int64_t k, const double* X, int64
     default: return cudaErrorInvalidValue;              \
   }
 
-// Same for the tile width BN (the GEMM kernel template argument).
-#define BG_DISPATCH_BN(bn, ...)                         \
-  switch (bn) {                                         \
-    case 128: { constexpr int BNV = 128; __VA_ARGS__; } \
-    case 96: { constexpr int BNV = 96; __VA_ARGS__; }   \
-    case 80: { constexpr int BNV = 80; __VA_ARGS__; }   \
-    case 64: { constexpr int BNV = 64; __VA_ARGS__; }   \
-    case 48: { constexpr int BNV = 48; __VA_ARGS__; }   \
-    case 32: { constexpr int BNV = 32; __VA_ARGS__; }   \
-    default: return cudaErrorInvalidValue;              \
+// Same for the GEMM kernel template arguments: the tile width BN (from s)
+// and the compile-time slice count (3, 6 and 9 have unrolled versions).
+#define BG_DISPATCH_GEMM(s, ...)                                           \
+  switch (s) {                                                             \
+    case 3: { constexpr int BNV = 128, SFV = 3; __VA_ARGS__; }             \
+    case 6: { constexpr int BNV = 80, SFV = 6; __VA_ARGS__; }              \
+    case 9: { constexpr int BNV = 48, SFV = 9; __VA_ARGS__; }              \
+    case 1: case 2: case 4: { constexpr int BNV = 128, SFV = 0; __VA_ARGS__; } \
+    case 5: { constexpr int BNV = 96, SFV = 0; __VA_ARGS__; }              \
+    case 7: case 8: { constexpr int BNV = 64, SFV = 0; __VA_ARGS__; }      \
+    case 10: { constexpr int BNV = 48, SFV = 0; __VA_ARGS__; }             \
+    case 11: case 12: { constexpr int BNV = 32, SFV = 0; __VA_ARGS__; }    \
+    default: return cudaErrorInvalidValue;                                 \
   }
 
 }  // namespace
@@ -1339,20 +1353,20 @@ static void finish_desc(SplitPlan* p) {
   p->desc = buf;
 }
 
-static cudaError_t set_gemm_attr(int bn) {
-  static bool done[6] = {false, false, false, false, false, false};
-  const int slot = bn == 128 ? 0 : bn == 96 ? 1 : bn == 80 ? 2 : bn == 64 ? 3 : bn == 48 ? 4 : 5;
-  if (done[slot]) return cudaSuccess;
-  BG_DISPATCH_BN(bn, {
-    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<BNV>,
+static cudaError_t set_gemm_attr(int s) {
+  static bool done[kMaxSlices + 1] = {};
+  if (s < 1 || s > kMaxSlices) return cudaErrorInvalidValue;
+  if (done[s]) return cudaSuccess;
+  BG_DISPATCH_GEMM(s, {
+    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<BNV, SFV>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-    if (e == cudaSuccess) done[slot] = true;
+    if (e == cudaSuccess) done[s] = true;
     return e;
   });
 }
 
 static void grids(SplitPlan* p) {
-  set_gemm_attr(p->bn);
+  set_gemm_attr(p->s);
   p->grid_gemm = (int)std::max<int64_t>(1, std::min<int64_t>(p->sms, p->n_units));
   int bps = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, split_slice_kernel<9>, kSliceThreads, 0);
@@ -1438,8 +1452,8 @@ static cudaError_t launch_gemm(SplitPlan* p, void* C, const Scalars& sc, const i
   g.kpass = p->kpass;
   g.a_stages = p->a_stages;
   g.err = d_err;
-  BG_DISPATCH_BN(p->bn, {
-    split_gemm_kernel<BNV><<<p->grid_gemm, kGemmThreads, p->smem, st>>>(g);
+  BG_DISPATCH_GEMM(p->s, {
+    split_gemm_kernel<BNV, SFV><<<p->grid_gemm, kGemmThreads, p->smem, st>>>(g);
     count_launch();
     return cudaGetLastError();
   });

@@ -383,6 +383,56 @@ __device__ __forceinline__ uint32_t bf16_of_int(int d) {
   return __float_as_uint(f) >> 16;
 }
 
+// Digits of round(x 2^(S BETA - e)) with S and BETA known at compile time
+// and S BETA <= 60 (the cut the slice kernels use for the documented modes):
+// the same balanced digits as make_digits, read from the two 32-bit halves
+// of the biased 64-bit fixed-point value with constant shifts, each turned
+// straight into its FP32 value f[p] (exact: |d| <= 256). Returns |d_1| + 0.51,
+// an upper bound of the absolute digit weight sum_p |d_p| 2^(-BETA (p-1))
+// (the lower digits add at most 2^(BETA-1) sum_{j>=1} 2^(-BETA j) < 0.51).
+template <int S, int BETA>
+__device__ __forceinline__ float make_digits_f(double x, int e, long long bias, float* f) {
+  static_assert(S * BETA <= 60, "narrow cut only");
+  constexpr int HALF = 1 << (BETA - 1), MASK = (1 << BETA) - 1;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int eb = (int)(bits >> 52) & 0x7FF;
+  unsigned long long M = bits & ((1ull << 52) - 1);
+  int q;
+  if (eb == 0) {
+    q = -1074;
+  } else {
+    M |= 1ull << 52;
+    q = eb - 1075;
+  }
+  const int sh = q - e + S * BETA;
+  unsigned long long N = 0;
+  if (M != 0) {
+    if (sh >= 0) N = M << sh;
+    else if (sh > -64) N = (M + (1ull << (-sh - 1))) >> (-sh);
+  }
+  const long long Np = ((bits >> 63) ? -(long long)N : (long long)N) + bias;
+  const uint32_t lo = (uint32_t)Np, hi = (uint32_t)((unsigned long long)Np >> 32);
+  // f = float(field - HALF) = as_float(0x4B400000 + field - HALF) - 1.5 * 2^23
+  constexpr int kMagic = 0x4B400000 - HALF;
+#pragma unroll
+  for (int p = S - 1; p >= 1; --p) {
+    constexpr int dummy = 0;
+    (void)dummy;
+    const int off = BETA * (S - 1 - p);
+    uint32_t field;
+    if (off + BETA <= 32) field = (lo >> off) & MASK;
+    else if (off >= 32) field = (hi >> (off - 32)) & MASK;
+    else field = __funnelshift_r(lo, hi, off) & MASK;
+    f[p] = __int_as_float(kMagic + (int)field) - 12582912.0f;
+  }
+  constexpr int off0 = BETA * (S - 1);
+  int top;
+  if (off0 >= 32) top = (int)hi >> (off0 - 32);
+  else top = (int)__funnelshift_r(lo, hi, off0) | 0;  // |value| < 2^31 after the shift
+  f[0] = __int_as_float(kMagic + top) - 12582912.0f;
+  return fabsf(f[0]) + 0.51f;
+}
+
 // Norm exponent: smallest R with sqrt(S) < 2^R (with a margin for the FP32
 // rounding of S); -126 for S == 0.
 __device__ __forceinline__ int norm_exponent(float S) {
@@ -413,174 +463,157 @@ __device__ __forceinline__ double valB(const double* B, const SInst& in, int cpl
 // Tile layout (A and B alike): the tile of plane p (0-based) and k-block kb
 // of a block is tile number tile0 + kb * S + p; tiles are `lines` rows of 128
 // bytes (64 BF16 values of k), chunk c of row r stored at chunk c ^ (r & 7).
-template <int S>
+//
+// Work distribution: the (group of 4 lines) x (k-block) items of a block are
+// dealt to the CTA's warps; a warp covers 4 lines x 8 chunks of 8 k values,
+// so each plane store writes 4 whole 128-byte rows (512 contiguous bytes)
+// and every lane keeps 8 loads in flight. Line maxima and norm sums meet in
+// shared memory through integer atomics (max, and sums of fixed-point
+// squares), so the result does not depend on the order of the items.
+
+// The 8 values x[u] = line `line`, k = q0 + u of the block's operand (A rows
+// or B columns; complex A through its 2 x 2 real expansion), 0 beyond k' or
+// for an invalid line.
+__device__ __forceinline__ void load8(const SliceArgs& a, bool isA, const SInst& in, bool valid,
+                                      int line, int q0, int kv, double (&x)[8]) {
+  if (!valid) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = 0.0;
+    return;
+  }
+  if (isA) {
+    if (!a.cplx) {
+      const double* p = a.A + in.a_off + line + (int64_t)q0 * in.lda;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = q0 + u < kv ? __ldg(p + (int64_t)u * in.lda) : 0.0;
+    } else {
+      const double2* p = reinterpret_cast<const double2*>(a.A) + in.a_off + (line >> 1) +
+                         (int64_t)(q0 >> 1) * in.lda;
+      const bool im_row = line & 1;
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        const double2 z = q0 + u < kv ? __ldg(p + (int64_t)(u >> 1) * in.lda) : make_double2(0.0, 0.0);
+        // row 2r: (re, -im); row 2r+1: (im, re)
+        x[u] = im_row ? z.y : z.x;
+        x[u + 1] = q0 + u + 1 < kv ? (im_row ? z.x : -z.y) : 0.0;
+      }
+    }
+  } else {
+    const double* p = a.cplx ? a.B + 2 * in.b_off + q0 + (int64_t)line * 2 * in.ldb
+                             : a.B + in.b_off + q0 + (int64_t)line * in.ldb;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = q0 + u < kv ? __ldg(p + u) : 0.0;
+  }
+}
+
+// BETA > 0: compile-time digit width (S * BETA <= 60); BETA == 0: any width a.beta.
+template <int S, int BETA>
 __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceArgs a) {
-  const DigitCtx dc = digit_ctx<S>(a.beta);
-  __shared__ unsigned long long s_max[2][128];
-  __shared__ float s_n2[2][128];
+  const DigitCtx dc = digit_ctx<S>(BETA > 0 ? BETA : a.beta);
+  __shared__ unsigned long long s_max[128];
+  __shared__ unsigned long long s_n2[128];  // sum of alpha^2 in units of 2^-8 (rounded up)
   __shared__ int s_e[128];
   __shared__ int s_R[128];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int cc = lane & 7;        // chunk of 8 k values inside a 64-wide k-block
+  const int lsub = lane >> 3;     // line within the warp's group of 4
+  constexpr int kWarps = kSliceThreads / 32;
   for (int64_t jb = blockIdx.x; jb < a.njobs; jb += gridDim.x) {
     const SliceJob J = a.jobs[jb];
     const bool isA = J.side == 0;
     const int kv = J.kv;
     const int lines = isA ? BM : a.bn;
+    const int groups = lines / 4;
+    const int items = groups * J.nkb;
     const int tile_bytes = lines * kLineBytes;
     uint8_t* tiles = isA ? a.tilesA : a.tilesB;
-    // ---- phase 1: line maxima
-    if (isA) {
-      const int l = t & 127, h = t >> 7;
-      const int li = l / J.span;
-      unsigned long long mx = 0;
-      if (li < J.g) {
-        const SInst in = a.instA[a.orderA[J.pos + li]];
-        const int r = J.org + l % J.span;
-        const int mv = a.cplx ? 2 * in.m : in.m;
-        if (r < mv)
-          for (int q = h; q < kv; q += 2) {
-            const unsigned long long b =
-                (unsigned long long)__double_as_longlong(valA(a.A, in, a.cplx, r, q)) &
-                0x7FFFFFFFFFFFFFFFull;
-            mx = b > mx ? b : mx;
-          }
-      }
-      s_max[h][l] = mx;
-    } else {
-      for (int l = warp * 16; l < warp * 16 + 16; ++l) {
-        const int li = l / J.span;
-        unsigned long long mx = 0;
-        if (l < lines && li < J.g) {
-          const SInst in = a.instB[a.orderB[J.pos + li]];
-          const int c = J.org + l % J.span;
-          if (c < in.n)
-            for (int q = lane; q < kv; q += 32) {
-              const unsigned long long b =
-                  (unsigned long long)__double_as_longlong(valB(a.B, in, a.cplx, q, c)) &
-                  0x7FFFFFFFFFFFFFFFull;
-              mx = b > mx ? b : mx;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
-          mx = y > mx ? y : mx;
-        }
-        if (lane == 0) {
-          s_max[0][l] = mx;
-          s_max[1][l] = 0;
-        }
-      }
-    }
-    __syncthreads();
     if (t < 128) {
-      const unsigned long long m0 = s_max[0][t], m1 = s_max[1][t];
-      s_e[t] = line_exponent(m0 > m1 ? m0 : m1);
+      s_max[t] = 0;
+      s_n2[t] = 0;
     }
     __syncthreads();
-    // ---- phase 2: digit planes
-    int d[S];
-    if (isA) {
-      const int l = t & 127, h = t >> 7;
+    // ---- phase 1: line maxima (exponents)
+    for (int wi = warp; wi < items; wi += kWarps) {
+      const int l = (wi % groups) * 4 + lsub, kb = wi / groups;
       const int li = l / J.span;
-      const bool lvalid = li < J.g;
+      const int line = J.org + l % J.span;
       SInst in{};
-      int r = 0, mv = 0;
-      if (lvalid) {
-        in = a.instA[a.orderA[J.pos + li]];
-        r = J.org + l % J.span;
-        mv = a.cplx ? 2 * in.m : in.m;
+      bool valid = li < J.g;
+      if (valid) {
+        in = isA ? a.instA[a.orderA[J.pos + li]] : a.instB[a.orderB[J.pos + li]];
+        valid = isA ? line < (a.cplx ? 2 * in.m : in.m) : line < in.n;
       }
-      const bool rvalid = lvalid && r < mv;
+      double x[8];
+      load8(a, isA, in, valid, line, kb * BK + 8 * cc, kv, x);
+      unsigned long long mx = 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(x[u]) & 0x7FFFFFFFFFFFFFFFull;
+        mx = b > mx ? b : mx;
+      }
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+        mx = y > mx ? y : mx;
+      }
+      if (cc == 0 && mx) atomicMax(&s_max[l], mx);
+    }
+    __syncthreads();
+    if (t < 128) s_e[t] = line_exponent(s_max[t]);
+    __syncthreads();
+    // ---- phase 2: digit planes and the norm of the absolute digit weights
+    for (int wi = warp; wi < items; wi += kWarps) {
+      const int l = (wi % groups) * 4 + lsub, kb = wi / groups;
+      const int li = l / J.span;
+      const int line = J.org + l % J.span;
+      SInst in{};
+      bool valid = li < J.g;
+      if (valid) {
+        in = isA ? a.instA[a.orderA[J.pos + li]] : a.instB[a.orderB[J.pos + li]];
+        valid = isA ? line < (a.cplx ? 2 * in.m : in.m) : line < in.n;
+      }
       const int e = s_e[l];
-      float n2 = 0.f;
-      for (int kb = 0; kb < J.nkb; ++kb) {
-        for (int i = 0; i < 4; ++i) {
-          const int cc = h + 2 * i;
-          uint32_t w[S][4];
+      double x[8];
+      load8(a, isA, in, valid, line, kb * BK + 8 * cc, kv, x);
+      uint32_t w[S][4];
+      float n2f = 0.f;
 #pragma unroll
-          for (int u = 0; u < 8; u += 2) {
-            const int q0 = kb * BK + 8 * cc + u;
-            const double x0 = (rvalid && q0 < kv) ? valA(a.A, in, a.cplx, r, q0) : 0.0;
-            const double x1 = (rvalid && q0 + 1 < kv) ? valA(a.A, in, a.cplx, r, q0 + 1) : 0.0;
-            int d1[S];
-            const float al0 = make_digits<S>(x0, e, dc, d);
-            const float al1 = make_digits<S>(x1, e, dc, d1);
-            n2 = fmaf(al0, al0, n2);
-            n2 = fmaf(al1, al1, n2);
-#pragma unroll
-            for (int p = 0; p < S; ++p)
-              w[p][u >> 1] = bf16_of_int(d[p]) | (bf16_of_int(d1[p]) << 16);
-          }
-          uint8_t* dst = tiles + (J.tile0 + (int64_t)kb * S) * tile_bytes + l * kLineBytes +
-                         ((cc ^ (l & 7)) << 4);
+      for (int u = 0; u < 8; u += 2) {
+        float al0, al1;
+        if constexpr (BETA > 0) {
+          float f0[S], f1[S];
+          al0 = make_digits_f<S, BETA>(x[u], e, dc.bias64, f0);
+          al1 = make_digits_f<S, BETA>(x[u + 1], e, dc.bias64, f1);
 #pragma unroll
           for (int p = 0; p < S; ++p)
-            *reinterpret_cast<uint4*>(dst + (int64_t)p * tile_bytes) =
-                make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+            w[p][u >> 1] = __byte_perm(__float_as_uint(f0[p]), __float_as_uint(f1[p]), 0x7632);
+        } else {
+          int d0[S], d1[S];
+          al0 = make_digits<S>(x[u], e, dc, d0);
+          al1 = make_digits<S>(x[u + 1], e, dc, d1);
+#pragma unroll
+          for (int p = 0; p < S; ++p) w[p][u >> 1] = bf16_of_int(d0[p]) | (bf16_of_int(d1[p]) << 16);
         }
+        n2f = fmaf(al0, al0, n2f);
+        n2f = fmaf(al1, al1, n2f);
       }
-      s_n2[h][l] = n2;
-    } else {
-      float n2[4] = {0.f, 0.f, 0.f, 0.f};
-      const int cc = lane & 7;
-      for (int kb = 0; kb < J.nkb; ++kb) {
+      uint8_t* dst = tiles + (J.tile0 + (int64_t)kb * S) * tile_bytes + l * kLineBytes +
+                     ((cc ^ (l & 7)) << 4);
 #pragma unroll
-        for (int it = 0; it < 4; ++it) {
-          const int l = it * 32 + warp * 4 + (lane >> 3);
-          const int li = l / J.span;
-          bool cvalid = false;
-          SInst in{};
-          int c = 0;
-          if (l < lines && li < J.g) {
-            in = a.instB[a.orderB[J.pos + li]];
-            c = J.org + l % J.span;
-            cvalid = c < in.n;
-          }
-          const int e = s_e[l];
-          uint32_t w[S][4];
+      for (int p = 0; p < S; ++p)
+        *reinterpret_cast<uint4*>(dst + (int64_t)p * tile_bytes) =
+            make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+      // 8 values of at most 257.51^2 each, in units of 2^-8: < 2^28 per lane; 8 lanes < 2^31
+      uint32_t n2 = __float2uint_ru(n2f * 256.0f * 1.0001f);
 #pragma unroll
-          for (int u = 0; u < 8; u += 2) {
-            const int q0 = kb * BK + 8 * cc + u;
-            const double x0 = (cvalid && q0 < kv) ? valB(a.B, in, a.cplx, q0, c) : 0.0;
-            const double x1 = (cvalid && q0 + 1 < kv) ? valB(a.B, in, a.cplx, q0 + 1, c) : 0.0;
-            int d1[S];
-            const float al0 = make_digits<S>(x0, e, dc, d);
-            const float al1 = make_digits<S>(x1, e, dc, d1);
-            n2[it] = fmaf(al0, al0, n2[it]);
-            n2[it] = fmaf(al1, al1, n2[it]);
-#pragma unroll
-            for (int p = 0; p < S; ++p)
-              w[p][u >> 1] = bf16_of_int(d[p]) | (bf16_of_int(d1[p]) << 16);
-          }
-          if (l < lines) {
-            uint8_t* dst = tiles + (J.tile0 + (int64_t)kb * S) * tile_bytes + l * kLineBytes +
-                           ((cc ^ (l & 7)) << 4);
-#pragma unroll
-            for (int p = 0; p < S; ++p)
-              *reinterpret_cast<uint4*>(dst + (int64_t)p * tile_bytes) =
-                  make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
-          }
-        }
-      }
-#pragma unroll
-      for (int it = 0; it < 4; ++it) {
-        float v = n2[it];
-        v += __shfl_xor_sync(0xFFFFFFFFu, v, 1);
-        v += __shfl_xor_sync(0xFFFFFFFFu, v, 2);
-        v += __shfl_xor_sync(0xFFFFFFFFu, v, 4);
-        const int l = it * 32 + warp * 4 + (lane >> 3);
-        if (cc == 0) {
-          s_n2[0][l] = v;
-          s_n2[1][l] = 0.f;
-        }
-      }
+      for (int o = 1; o < 8; o <<= 1) n2 += __shfl_xor_sync(0xFFFFFFFFu, n2, o);
+      if (cc == 0 && n2) atomicAdd(&s_n2[l], (unsigned long long)n2);
     }
     __syncthreads();
     // ---- phase 3: meta (exponent, norm exponent, block max of the norm exponent)
     int32_t* meta = (isA ? a.metaA : a.metaB) + (int64_t)J.blk * kMetaStride;
     if (t < 128) {
-      const int R = t < lines ? norm_exponent(s_n2[0][t] + s_n2[1][t]) : -126;
+      const int R = t < lines ? norm_exponent((float)s_n2[t] * (1.0f / 256.0f)) : -126;
       s_R[t] = R;
       meta[t] = s_e[t];
       meta[128 + t] = R;
@@ -1369,7 +1402,7 @@ static void grids(SplitPlan* p) {
   set_gemm_attr(p->s);
   p->grid_gemm = (int)std::max<int64_t>(1, std::min<int64_t>(p->sms, p->n_units));
   int bps = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, split_slice_kernel<9>, kSliceThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, split_slice_kernel<9, 6>, kSliceThreads, 0);
   if (bps < 1) bps = 1;
   p->grid_slice = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)p->sms * bps, p->n_jobs));
 }
@@ -1419,11 +1452,22 @@ static cudaError_t launch_slicer(SplitPlan* p, const SliceJob* jobs, int64_t njo
   a.beta = p->beta;
   a.bn = p->bn;
   const int grid = (int)std::min<int64_t>(p->grid_slice, njobs);
-  BG_DISPATCH_SLICES(p->s, {
-    split_slice_kernel<S><<<grid, kSliceThreads, 0, st>>>(a);
-    count_launch();
-    return cudaGetLastError();
-  });
+  // compile-time (slices, digit width) versions for the documented modes
+  if (p->s == 3 && p->beta == 7) {
+    split_slice_kernel<3, 7><<<grid, kSliceThreads, 0, st>>>(a);
+  } else if (p->s == 6 && p->beta == 7) {
+    split_slice_kernel<6, 7><<<grid, kSliceThreads, 0, st>>>(a);
+  } else if (p->s == 9 && p->beta == 6) {
+    split_slice_kernel<9, 6><<<grid, kSliceThreads, 0, st>>>(a);
+  } else {
+    BG_DISPATCH_SLICES(p->s, {
+      split_slice_kernel<S, 0><<<grid, kSliceThreads, 0, st>>>(a);
+      count_launch();
+      return cudaGetLastError();
+    });
+  }
+  count_launch();
+  return cudaGetLastError();
 }
 
 static cudaError_t launch_gemm(SplitPlan* p, void* C, const Scalars& sc, const int32_t* idx,

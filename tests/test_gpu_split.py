@@ -66,9 +66,13 @@ def test_nine_slices_within_fp64_envelope(gpu):
 
 @pytest.mark.parametrize("dtype", ["r64", "c128"])
 @pytest.mark.parametrize("n", [16, 48, 64, 130, 256])
-def test_exact_on_representable_inputs(gpu, dtype, n):
-    """Entries d * 2^j with |d| < 2^7 are cut exactly into 3 planes; every product
-    and sum then fits FP64 exactly, so the result must equal the oracle bit for bit."""
+@pytest.mark.parametrize("s,beta", [(3, 8), (3, 0), (6, 0), (9, 0)])
+def test_exact_on_representable_inputs(gpu, dtype, n, s, beta):
+    """Entries d * 2^j with |d| < 2^7 and one power of two per row of A / column of B
+    are cut exactly into the digit planes (at least 21 bits per line); every
+    product and sum then fits FP64 exactly, so the result must equal the oracle
+    bit for bit. beta = 0 takes the library's default width, i.e. the
+    compile-time digit cut of the documented modes."""
     rng = np.random.default_rng(n)
     count = 6
     shapes = [(n, n, n)] * count
@@ -91,7 +95,7 @@ def test_exact_on_representable_inputs(gpu, dtype, n):
         bb *= (2.0 ** rng.integers(-20, 20, n))[None, :]
         B[bo:bo + n * n] = bb.T.ravel()
     b = synth.Batch("exact", dtype, table, A, B, C, 1.0, 0.0)
-    Cg, _ = run_grouped(b, split(3, 8))
+    Cg, _ = run_grouped(b, split(s, beta))
     assert np.array_equal(host(Cg), oracle_batch(b))
 
 

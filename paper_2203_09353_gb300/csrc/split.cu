@@ -969,33 +969,44 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
           if (lane == 0) mbar_arrive(&S.tmem_free);
           ++passc;
         }
-        // ---- exact conversion, alpha/beta, store (TMEM already free: overlaps the next MMAs)
+        // ---- exact conversion, alpha/beta, store (TMEM already free: overlaps the next MMAs).
+        // Each group of 8 columns first loads its 8 old C values and 8 column
+        // exponents, then converts and stores: all loads are in flight together
+        // instead of each one waiting behind the previous column's store.
         const bool first_pass = c == 0;
+        const bool need_c = !first_pass || !g.sc.beta_zero;
         for (int j0 = 0; j0 < COLS; j0 += 8) {
+          double cv[8];
+          int fj[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int col = col0 + j0 + j;
             const bool valid = rvalid && col >= cmin && col < cmax;
-            const int cc = col + coff;
-            const double x = valid ? fixed_to_double(acc[j], Ebase + mb[col]) : 0.0;
-            double* cp = g.C + cbase + (int64_t)cc * ldcv;
+            fj[j] = __ldg(mb + col);
+            cv[j] = (valid && need_c) ? g.C[cbase + (int64_t)(col + coff) * ldcv] : 0.0;
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int col = col0 + j0 + j;
+            const bool valid = rvalid && col >= cmin && col < cmax;
+            const double x = valid ? fixed_to_double(acc[j], Ebase + fj[j]) : 0.0;
+            double* cp = g.C + cbase + (int64_t)(col + coff) * ldcv;
             if (!g.cplx) {
               if (valid) {
                 double v = alpha_one ? x : g.sc.alpha_re * x;
-                if (!first_pass) v += *cp;
-                else if (!g.sc.beta_zero) v = fma(g.sc.beta_re, *cp, v);
+                if (!first_pass) v += cv[j];
+                else if (!g.sc.beta_zero) v = fma(g.sc.beta_re, cv[j], v);
                 *cp = v;
               }
             } else {
               const double xp = __shfl_xor_sync(0xFFFFFFFFu, x, 1);
-              const bool need_c = valid && (!first_pass || !g.sc.beta_zero);
-              const double cv = need_c ? *cp : 0.0;
-              const double cpn = __shfl_xor_sync(0xFFFFFFFFu, cv, 1);
+              const double cpn = __shfl_xor_sync(0xFFFFFFFFu, cv[j], 1);
               if (valid) {
                 const double sgn = (rr & 1) ? 1.0 : -1.0;  // im row: +, re row: -
                 double v = fma(g.sc.alpha_re, x, sgn * g.sc.alpha_im * xp);
-                if (!first_pass) v += cv;
-                else if (!g.sc.beta_zero) v = fma(g.sc.beta_re, cv, fma(sgn * g.sc.beta_im, cpn, v));
+                if (!first_pass) v += cv[j];
+                else if (!g.sc.beta_zero)
+                  v = fma(g.sc.beta_re, cv[j], fma(sgn * g.sc.beta_im, cpn, v));
                 *cp = v;
               }
             }

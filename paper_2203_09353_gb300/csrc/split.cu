@@ -58,405 +58,13 @@
 #include <string>
 #include <vector>
 
-#include "split.h"
+#include "split_common.cuh"
 
 namespace bg {
 
+using namespace splitk;
+
 namespace {
-
-constexpr int BM = 128, BK = 64;
-constexpr int kATileBytes = BM * BK * 2;  // 16 KiB: one A plane of one k-block
-constexpr int kLineBytes = BK * 2;        // 128 bytes: one row of a tile
-constexpr int kMaxAStages = 8;
-constexpr int kGemmThreads = 320;
-constexpr int kEpiWarps = 8;
-constexpr int kMetaStride = 264;  // int32 per block: e[128], R[128], max R at [256]
-constexpr int kTmemCols = 512;
-constexpr int kSliceThreads = 256;
-constexpr int kMaxDynSmem = 232448;
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any single wait
-
-// Tile width (columns of the output tile, rows of a B tile) for s planes:
-// the largest multiple of 16 (at most 128) with s * BN <= 512 TMEM columns.
-__host__ __device__ constexpr int bn_for(int s) {
-  return s <= 4 ? 128 : s == 5 ? 96 : s == 6 ? 80 : s <= 8 ? 64 : s <= 10 ? 48 : 32;
-}
-
-struct SInst {
-  int64_t a_off, b_off, c_off;  // user element offsets
-  int64_t lda, ldb, ldc;        // user elements
-  int32_t m, n, k;              // user sizes
-  int32_t pad;
-};
-
-struct SliceJob {
-  int64_t tile0;  // first tile of the block (k-block 0, plane 1)
-  int32_t blk;    // block id = meta index
-  int32_t pos;    // first position in the order list
-  int16_t side;   // 0: A block (rows), 1: B block (columns)
-  int16_t g;      // instances stacked in the block
-  int16_t span;   // lines per stacked instance (virtual rows of A / columns of B)
-  int16_t nkb;    // k-blocks of 64
-  int32_t org;    // first line of the block within its instance (big instances)
-  int32_t kv;     // virtual k' of the instances
-};
-
-struct SplitUnit {
-  int64_t a_tile0, b_tile0;  // first tiles (chain mode: a_tile0 is relative to the pool entry)
-  int32_t a_blk, b_blk;      // meta blocks (chain mode: a_blk is the row block index)
-  int32_t pos;               // order position of the (first) instance
-  int16_t g;                 // packed instances (1 = a tile of one instance)
-  int16_t nkb;               // k-blocks
-  int16_t kmma_last;         // MMA K-steps (16 each) in the last k-block
-  int16_t mrow;              // virtual rows per packed instance
-  int16_t ncol;              // columns per packed instance
-  int16_t pad;
-  int32_t r0, c0;            // tile origin in the instance (virtual rows, columns)
-};
-
-struct SliceArgs {
-  const SliceJob* jobs;
-  int64_t njobs;
-  const SInst* instA;
-  const SInst* instB;
-  const int32_t* orderA;
-  const int32_t* orderB;
-  const double* A;
-  const double* B;
-  uint8_t* tilesA;
-  uint8_t* tilesB;
-  int32_t* metaA;
-  int32_t* metaB;
-  int cplx, s, beta, bn;
-};
-
-struct GemmArgs {
-  const SplitUnit* units;
-  int64_t nunits;
-  const SInst* inst;
-  const int32_t* order;
-  const uint8_t* tilesA;
-  const uint8_t* tilesB;
-  const int32_t* metaA;
-  const int32_t* metaB;
-  double* C;
-  const int32_t* idx;         // chain mode: pool index per walker, else nullptr
-  const int64_t* pool_tile0;  // chain mode: first tile of each pool entry
-  const int32_t* pool_blk0;   // chain mode: first meta block of each pool entry
-  const SInst* pool;          // chain mode: pool entries (sizes)
-  int32_t pool_count;         // chain mode: number of pool entries
-  Scalars sc;
-  int cplx, s, beta, skip_product;
-  int kpass;                  // k-blocks per exact pass
-  int a_stages;               // slots of the A ring
-  int* err;
-};
-
-// ---- small device helpers --------------------------------------------------------------
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void record_error(int* err, int code, int loc, int detail) {
-  if (atomicCAS(err, 0, code) == 0) {
-    err[1] = loc;
-    err[2] = detail;
-  }
-  atomicAdd(err + 3, 1);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Waits for the phase with the given parity; gives up (returns false) after
-// kWaitNs or when another role has raised the abort flag.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
-                                          const volatile int* abort_flag) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long deadline = globaltimer_ns() + kWaitNs;
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
-    if (globaltimer_ns() > deadline) return false;
-  }
-  return true;
-}
-
-// Waits for the phase with the given parity for at most kWaitNs, ignoring the
-// abort flag (used to let in-flight copies and MMAs finish before exit).
-__device__ __forceinline__ bool mbar_wait_time(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long deadline = globaltimer_ns() + kWaitNs;
-  while (!mbar_try_wait(bar, parity))
-    if (globaltimer_ns() > deadline) return false;
-  return true;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (the layout the slicer writes).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
-  return d;
-}
-
-// Instruction descriptor: kind::f16, A = B = BF16, D = FP32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.u32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_ld_wait() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// ---- digits --------------------------------------------------------------------------------
-
-// Exponent e with |x| < 2^e for the largest magnitude of a line, from the bit
-// pattern of that magnitude (0 for an all-zero line).
-__device__ __forceinline__ int line_exponent(unsigned long long maxbits) {
-  if (maxbits == 0) return 0;
-  const int eb = (int)(maxbits >> 52) & 0x7FF;
-  if (eb != 0) return eb - 1022;
-  const unsigned long long frac = maxbits & ((1ull << 52) - 1);
-  return (64 - __clzll((long long)frac)) - 1074;
-}
-
-// Per-kernel constants of the digit cut: digit width beta, half = 2^(beta-1),
-// the balancing bias sum_{p=1..S} half 2^(beta (S-p)) and 2^-beta.
-struct DigitCtx {
-  int beta, half, mask;
-  bool narrow;  // S beta <= 60: the fixed-point value fits 64-bit arithmetic
-  long long bias64;
-  __int128 bias;
-  float step;
-};
-
-template <int S>
-__device__ __forceinline__ DigitCtx digit_ctx(int beta) {
-  DigitCtx c;
-  c.beta = beta;
-  c.half = 1 << (beta - 1);
-  c.mask = (1 << beta) - 1;
-  c.narrow = S * beta <= 60;
-  c.bias = 0;
-#pragma unroll
-  for (int p = 0; p < S; ++p) c.bias = (c.bias << beta) + c.half;
-  c.bias64 = (long long)c.bias;
-  c.step = __int_as_float((127 - beta) << 23);
-  return c;
-}
-
-// Balanced base-2^beta digits of round(x 2^(S beta - e)), most significant
-// first: d[0] = d_1 ... d[S-1] = d_S, with |d_1| <= 2^beta and
-// -2^(beta-1) <= d_p < 2^(beta-1) for p >= 2. The magnitude is rounded half
-// up, then the sign applied; the balanced form comes from adding the bias
-// and reading beta-bit fields. Returns the absolute digit weight
-// alpha = sum_p |d_p| 2^(-beta (p-1)) (FP32) used for the norm bound.
-template <int S>
-__device__ __forceinline__ float make_digits(double x, int e, const DigitCtx& c, int* d) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const int eb = (int)(bits >> 52) & 0x7FF;
-  unsigned long long M = bits & ((1ull << 52) - 1);
-  int q;
-  if (eb == 0) {
-    q = -1074;
-  } else {
-    M |= 1ull << 52;
-    q = eb - 1075;
-  }
-  const int sh = q - e + S * c.beta;
-  const bool neg = (bits >> 63) != 0;
-  if (c.narrow) {
-    unsigned long long N = 0;
-    if (M != 0) {
-      if (sh >= 0) N = M << sh;
-      else if (sh > -64) N = (M + (1ull << (-sh - 1))) >> (-sh);
-    }
-    long long Np = (neg ? -(long long)N : (long long)N) + c.bias64;
-#pragma unroll
-    for (int p = S - 1; p >= 1; --p) {
-      d[p] = (int)(Np & c.mask) - c.half;
-      Np >>= c.beta;
-    }
-    d[0] = (int)Np - c.half;
-  } else {
-    unsigned __int128 N = 0;
-    if (M != 0) {
-      if (sh >= 0) N = (unsigned __int128)M << sh;
-      else if (sh > -64) N = (unsigned __int128)((M + (1ull << (-sh - 1))) >> (-sh));
-    }
-    __int128 Np = (neg ? -(__int128)N : (__int128)N) + c.bias;
-#pragma unroll
-    for (int p = S - 1; p >= 1; --p) {
-      d[p] = (int)((long long)Np & c.mask) - c.half;
-      Np >>= c.beta;
-    }
-    d[0] = (int)(long long)Np - c.half;
-  }
-  float alpha = 0.f, w = 1.f;
-#pragma unroll
-  for (int p = 0; p < S; ++p) {
-    alpha = fmaf((float)abs(d[p]), w, alpha);
-    w *= c.step;
-  }
-  return alpha;
-}
-
-// BF16 bit pattern of a small integer (|d| <= 256), exact.
-__device__ __forceinline__ uint32_t bf16_of_int(int d) {
-  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
-  return __float_as_uint(f) >> 16;
-}
-
-// Digits of round(x 2^(S BETA - e)) with S and BETA known at compile time
-// and S BETA <= 60 (the cut the slice kernels use for the documented modes):
-// the same balanced digits as make_digits, read from the two 32-bit halves
-// of the biased 64-bit fixed-point value with constant shifts, each turned
-// straight into its FP32 value f[p] (exact: |d| <= 256). Returns |d_1| + 0.51,
-// an upper bound of the absolute digit weight sum_p |d_p| 2^(-BETA (p-1))
-// (the lower digits add at most 2^(BETA-1) sum_{j>=1} 2^(-BETA j) < 0.51).
-template <int S, int BETA>
-__device__ __forceinline__ float make_digits_f(double x, int e, long long bias, float* f) {
-  static_assert(S * BETA <= 60, "narrow cut only");
-  constexpr int HALF = 1 << (BETA - 1), MASK = (1 << BETA) - 1;
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const int eb = (int)(bits >> 52) & 0x7FF;
-  unsigned long long M = bits & ((1ull << 52) - 1);
-  int q;
-  if (eb == 0) {
-    q = -1074;
-  } else {
-    M |= 1ull << 52;
-    q = eb - 1075;
-  }
-  const int sh = q - e + S * BETA;
-  unsigned long long N = 0;
-  if (M != 0) {
-    if (sh >= 0) N = M << sh;
-    else if (sh > -64) N = (M + (1ull << (-sh - 1))) >> (-sh);
-  }
-  const long long Np = ((bits >> 63) ? -(long long)N : (long long)N) + bias;
-  const uint32_t lo = (uint32_t)Np, hi = (uint32_t)((unsigned long long)Np >> 32);
-  // f = float(field - HALF) = as_float(0x4B400000 + field - HALF) - 1.5 * 2^23
-  constexpr int kMagic = 0x4B400000 - HALF;
-#pragma unroll
-  for (int p = S - 1; p >= 1; --p) {
-    constexpr int dummy = 0;
-    (void)dummy;
-    const int off = BETA * (S - 1 - p);
-    uint32_t field;
-    if (off + BETA <= 32) field = (lo >> off) & MASK;
-    else if (off >= 32) field = (hi >> (off - 32)) & MASK;
-    else field = __funnelshift_r(lo, hi, off) & MASK;
-    f[p] = __int_as_float(kMagic + (int)field) - 12582912.0f;
-  }
-  constexpr int off0 = BETA * (S - 1);
-  int top;
-  if (off0 >= 32) top = (int)hi >> (off0 - 32);
-  else top = (int)__funnelshift_r(lo, hi, off0) | 0;  // |value| < 2^31 after the shift
-  f[0] = __int_as_float(kMagic + top) - 12582912.0f;
-  return fabsf(f[0]) + 0.51f;
-}
-
-// Norm exponent: smallest R with sqrt(S) < 2^R (with a margin for the FP32
-// rounding of S); -126 for S == 0.
-__device__ __forceinline__ int norm_exponent(float S) {
-  if (!(S > 0.f)) return -126;
-  const float S2 = S * 1.03125f;
-  const int E = (int)((__float_as_uint(S2) >> 23) & 0xFF) - 126;
-  return (E + 1) >> 1;
-}
-
-// Value of the virtual real matrix A' (m' x k') at (r, q); A is real or
-// complex (expanded 2x2 per entry).
-__device__ __forceinline__ double valA(const double* A, const SInst& in, int cplx, int r, int q) {
-  if (!cplx) return __ldg(A + in.a_off + r + (int64_t)q * in.lda);
-  const double2 z =
-      __ldg(reinterpret_cast<const double2*>(A) + in.a_off + (r >> 1) + (int64_t)(q >> 1) * in.lda);
-  const int sel = ((r & 1) << 1) | (q & 1);
-  return sel == 0 ? z.x : sel == 1 ? -z.y : sel == 2 ? z.y : z.x;
-}
-
-// Value of B' (k' x n) at (q, c): the real view of B.
-__device__ __forceinline__ double valB(const double* B, const SInst& in, int cplx, int q, int c) {
-  if (!cplx) return __ldg(B + in.b_off + q + (int64_t)c * in.ldb);
-  return __ldg(B + 2 * in.b_off + q + (int64_t)c * 2 * in.ldb);
-}
 
 // ---- slicer ----------------------------------------------------------------------------------
 
@@ -630,404 +238,6 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
   }
 }
 
-// ---- GEMM --------------------------------------------------------------------------------------
-
-struct GemmBars {
-  uint64_t b_full[2];
-  uint64_t b_empty[2];
-  uint64_t a_full[kMaxAStages];
-  uint64_t a_empty[kMaxAStages];
-  uint64_t lvl_full[kMaxSlices];
-  uint64_t tmem_free;
-  uint64_t mma_done;
-  uint32_t tmem_base;
-  int abort_flag;
-};
-
-// Resolves the tiles and meta block of a unit. In chain mode the A side is
-// the pool matrix named by the walker's index for this step; an index out of
-// range or naming a matrix of another size makes the unit invalid (returns
-// false): every role then skips it and the walker's output is left as is.
-__device__ __forceinline__ bool unit_tiles(const GemmArgs& g, const SplitUnit& U, int64_t* at,
-                                           int64_t* bt, int* ablk) {
-  *bt = U.b_tile0;
-  if (g.idx) {
-    const int w = g.order[U.pos];
-    const int j = g.idx[w];
-    if (j < 0 || j >= g.pool_count || g.pool[j].n != g.inst[w].n) {
-      *at = 0;
-      *ablk = 0;
-      return false;
-    }
-    *at = g.pool_tile0[j] + U.a_tile0;
-    *ablk = g.pool_blk0[j] + U.a_blk;
-    return true;
-  }
-  *at = U.a_tile0;
-  *ablk = U.a_blk;
-  return true;
-}
-
-__device__ __forceinline__ int unit_passes(const GemmArgs& g, const SplitUnit& U) {
-  if (g.skip_product || U.nkb <= 0) return 0;
-  return (U.nkb + g.kpass - 1) / g.kpass;
-}
-
-// Exactly rounded FP64 value of a * 2^E (a a 64-bit integer), by integer
-// operations (round to nearest even), with FP64 scaling only outside the
-// normal range.
-__device__ __forceinline__ double fixed_to_double(long long a, int E) {
-  if (a == 0) return 0.0;
-  const unsigned long long sign = a < 0 ? (1ull << 63) : 0ull;
-  const unsigned long long u = a < 0 ? (unsigned long long)(-a) : (unsigned long long)a;
-  const int lz = __clzll((long long)u);
-  const unsigned long long un = u << lz;
-  unsigned long long mant = un >> 11;
-  const unsigned long long rem = un & 0x7FFull;
-  mant += (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
-  int ex = 63 - lz + E;
-  if (mant >> 53) {
-    mant >>= 1;
-    ex += 1;
-  }
-  const int biased = ex + 1023;
-  if (biased >= 1 && biased <= 2046)
-    return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) |
-                                            (mant & ((1ull << 52) - 1))));
-  const double v = scalbn((double)mant, ex - 52);
-  return sign ? -v : v;
-}
-
-// SF > 0: the slice count is the compile-time constant SF (the MMA issue loop
-// unrolls completely); SF == 0: any slice count g.s with this tile width.
-template <int BN, int SF>
-__global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmArgs g) {
-  constexpr int COLS = BN / 2;  // output columns per epilogue thread
-  constexpr int BTILE = BN * kLineBytes;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                             ~uintptr_t(1023));
-  const int s = SF > 0 ? SF : g.s;
-  const int bplanes_bytes = s * BTILE;
-  uint8_t* bbuf = smem;                          // 2 x s B tiles
-  uint8_t* aring = smem + 2 * bplanes_bytes;     // a_stages x 16 KiB
-  GemmBars& S = *reinterpret_cast<GemmBars*>(aring + g.a_stages * kATileBytes);
-  volatile int* abort_flag = &S.abort_flag;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int NA = g.a_stages;
-
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(&S.b_full[i], 1);
-      mbar_init(&S.b_empty[i], 1);
-    }
-    for (int i = 0; i < NA; ++i) {
-      mbar_init(&S.a_full[i], 1);
-      mbar_init(&S.a_empty[i], 1);
-    }
-    for (int i = 0; i < s; ++i) mbar_init(&S.lvl_full[i], 1);
-    mbar_init(&S.tmem_free, kEpiWarps);
-    mbar_init(&S.mma_done, 1);
-    S.abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&S.tmem_base)),
-                 "r"(kTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem_base = S.tmem_base;
-
-  if (warp == 0) {
-    // ---------------- producer: one TMA bulk copy of the s B planes per k-block, and
-    // the s A planes of the k-block through the A ring
-    if (lane == 0) {
-      uint32_t kbc = 0, afill = 0;
-      bool ok = true;
-      for (int64_t u = blockIdx.x; u < g.nunits && ok; u += gridDim.x) {
-        const SplitUnit U = g.units[u];
-        int64_t at, bt;
-        int ablk;
-        if (!unit_tiles(g, U, &at, &bt, &ablk)) continue;
-        const int npass = unit_passes(g, U);
-        for (int c = 0; c < npass && ok; ++c) {
-          const int kb_lo = c * g.kpass, kb_hi = min((int)U.nkb, kb_lo + g.kpass);
-          for (int kb = kb_lo; kb < kb_hi && ok; ++kb, ++kbc) {
-            const int buf = kbc & 1;
-            const uint32_t use = kbc >> 1;
-            if (use > 0 && !mbar_wait(&S.b_empty[buf], (use - 1) & 1, abort_flag)) {
-              record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_EMPTY_BARRIER, (int)u);
-              *abort_flag = 1;
-              ok = false;
-              break;
-            }
-            mbar_arrive_expect_tx(&S.b_full[buf], (uint32_t)bplanes_bytes);
-            bulk_g2s(bbuf + buf * bplanes_bytes, g.tilesB + (bt + (int64_t)kb * s) * BTILE,
-                     (uint32_t)bplanes_bytes, &S.b_full[buf]);
-            for (int p = 0; p < s; ++p, ++afill) {
-              const int slot = afill % NA;
-              const uint32_t ause = afill / NA;
-              if (ause > 0 && !mbar_wait(&S.a_empty[slot], (ause - 1) & 1, abort_flag)) {
-                record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_EMPTY_BARRIER, (int)u);
-                *abort_flag = 1;
-                ok = false;
-                break;
-              }
-              mbar_arrive_expect_tx(&S.a_full[slot], kATileBytes);
-              bulk_g2s(aring + slot * kATileBytes,
-                       g.tilesA + (at + (int64_t)kb * s + p) * kATileBytes, kATileBytes,
-                       &S.a_full[slot]);
-            }
-          }
-        }
-      }
-      // let every copy this thread started land before the CTA can exit
-      for (uint32_t j = kbc > 2 ? kbc - 2 : 0; j < kbc; ++j)
-        mbar_wait_time(&S.b_full[j & 1], (j >> 1) & 1);
-      for (uint32_t j = afill > (uint32_t)NA ? afill - NA : 0; j < afill; ++j)
-        mbar_wait_time(&S.a_full[j % NA], (j / NA) & 1);
-    }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer: one N-concatenated MMA per A plane and K-step
-    if (lane == 0) {
-      uint32_t kbc = 0, passc = 0;
-      int slot = 0;
-      uint32_t aphase = 0;
-      bool ok = true;
-      const uint32_t bbase = smem_u32(bbuf);
-      const uint32_t abase = smem_u32(aring);
-      for (int64_t u = blockIdx.x; u < g.nunits && ok; u += gridDim.x) {
-        const SplitUnit U = g.units[u];
-        int64_t at_, bt_;
-        int ablk_;
-        if (!unit_tiles(g, U, &at_, &bt_, &ablk_)) continue;
-        const int npass = unit_passes(g, U);
-        for (int c = 0; c < npass && ok; ++c, ++passc) {
-          if (passc > 0 && !mbar_wait(&S.tmem_free, (passc - 1) & 1, abort_flag)) {
-            record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_ACC_EMPTY, (int)u);
-            *abort_flag = 1;
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const int kb_lo = c * g.kpass, kb_hi = min((int)U.nkb, kb_lo + g.kpass);
-          for (int kb = kb_lo; kb < kb_hi && ok; ++kb, ++kbc) {
-            const int buf = kbc & 1;
-            if (!mbar_wait(&S.b_full[buf], (kbc >> 1) & 1, abort_flag)) {
-              record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_FULL_BARRIER, (int)u);
-              *abort_flag = 1;
-              ok = false;
-              break;
-            }
-            const uint64_t bdesc = sw128_desc(bbase + buf * bplanes_bytes);
-            const int nk = (kb == U.nkb - 1) ? U.kmma_last : 4;
-            const bool last_kb = kb == kb_hi - 1;
-            uint32_t acc0 = kb == kb_lo ? 0u : 1u;  // the first MMA of a pass initialises TMEM
-#pragma unroll
-            for (int p = 0; p < (SF > 0 ? SF : kMaxSlices); ++p) {
-              if (SF == 0 && p >= s) break;
-              if (!mbar_wait(&S.a_full[slot], aphase, abort_flag)) {
-                record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_FULL_BARRIER, (int)u);
-                *abort_flag = 1;
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-              const uint64_t adesc = sw128_desc(abase + slot * kATileBytes);
-              // B planes 1..s-p (levels p+2 .. s+1) as one N range, cut in pieces of <= 256
-              const int ncat = (s - p) * BN;
-              const int n1 = ncat > 256 ? ncat - 256 : 0;
-              const uint32_t id0 = make_idesc(BM, ncat > 256 ? 256 : ncat);
-              const uint32_t id1 = make_idesc(BM, n1 > 0 ? n1 : 16);
-              const uint32_t d0 = tmem_base + p * BN;
-              constexpr uint64_t kB256 = (256 * kLineBytes) >> 4;
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                if (kk < nk) {
-                  const uint32_t acc = kk == 0 ? acc0 : 1u;
-                  umma_bf16(d0, adesc + 2 * kk, bdesc + 2 * kk, id0, acc);
-                  if (n1 > 0) umma_bf16(d0 + 256, adesc + 2 * kk, bdesc + kB256 + 2 * kk, id1, acc);
-                }
-              }
-              acc0 = 1u;
-              umma_commit(&S.a_empty[slot]);
-              if (last_kb) umma_commit(&S.lvl_full[p]);  // level p+2 is complete
-              if (++slot == NA) {
-                slot = 0;
-                aphase ^= 1;
-              }
-            }
-            if (!ok) break;
-            umma_commit(&S.b_empty[buf]);
-          }
-        }
-      }
-      // all MMAs issued by this thread are complete once mma_done fires
-      umma_commit(&S.mma_done);
-      mbar_wait_time(&S.mma_done, 0);
-    }
-  } else {
-    // ---------------- epilogue: drain levels, recombine, free TMEM, store
-    const int quad = warp & 3;
-    const int half = (warp - 2) >> 2;
-    const int row = quad * 32 + lane;
-    const int col0 = half * COLS;
-    const uint32_t tq = tmem_base + ((uint32_t)(quad * 32) << 16) + col0;
-    const bool alpha_one = g.sc.alpha_re == 1.0 && g.sc.alpha_im == 0.0;
-    uint32_t passc = 0;
-    bool ok = true;
-    for (int64_t u = blockIdx.x; u < g.nunits && ok; u += gridDim.x) {
-      const SplitUnit U = g.units[u];
-      int64_t at, bt;
-      int ablk;
-      if (!unit_tiles(g, U, &at, &bt, &ablk)) {
-        if (warp == 2 && lane == 0)
-          record_error(g.err, BG_ERR_INVALID_ARG, ERRLOC_CHAIN_INDEX, (int)g.order[U.pos]);
-        continue;
-      }
-      const int32_t* ma = g.metaA + (int64_t)ablk * kMetaStride;
-      const int32_t* mb = g.metaB + (int64_t)U.b_blk * kMetaStride;
-      const int e_i = ma[row];
-      const int F = ma[128 + row] + mb[256] + 1;
-      // output rows/columns of this thread
-      int rr, inst_pos, cmin, cmax, coff;
-      bool rvalid;
-      if (U.g > 1) {
-        const int li = row / U.mrow;
-        rr = row - li * U.mrow;
-        rvalid = li < U.g;
-        inst_pos = U.pos + (rvalid ? li : 0);
-        cmin = li * U.ncol;
-        cmax = cmin + U.ncol;
-        coff = -cmin;
-      } else {
-        rr = U.r0 + row;
-        inst_pos = U.pos;
-        rvalid = true;
-        cmin = 0;
-        cmax = BN;
-        coff = U.c0;
-      }
-      const SInst in = g.inst[g.order[inst_pos]];
-      const int mv = g.cplx ? 2 * in.m : in.m;
-      rvalid = rvalid && rr < mv;
-      if (U.g == 1) cmax = min(cmax, in.n - U.c0);
-      const int64_t cbase = (g.cplx ? 2 * in.c_off : in.c_off) + rr;
-      const int64_t ldcv = g.cplx ? 2 * in.ldc : in.ldc;
-      const int Ebase = F - 62 + e_i - 2 * g.beta;
-      const int npass = unit_passes(g, U);
-      for (int c = 0; c < max(npass, 1) && ok; ++c) {
-        long long acc[COLS];
-#pragma unroll
-        for (int j = 0; j < COLS; ++j) acc[j] = 0;
-        if (npass > 0) {
-#pragma unroll 1
-          for (int lv = 0; lv < s; ++lv) {
-            bool got = true;
-            if (lane == 0) got = mbar_wait(&S.lvl_full[lv], passc & 1, abort_flag);
-            got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
-            if (!got) {
-              if (lane == 0) {
-                record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_ACC_FULL, (int)u);
-                *abort_flag = 1;
-              }
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            int sh = 62 - F - g.beta * lv;
-            sh = max(-63, min(62, sh));
-            const int lsh = sh > 0 ? sh : 0, rsh = sh < 0 ? -sh : 0;
-            const long long rnd = rsh > 0 ? (1ll << (rsh - 1)) : 0ll;
-#pragma unroll
-            for (int j0 = 0; j0 < COLS; j0 += 16) {
-              uint32_t v0[8], v1[8];
-              tmem_ld8(tq + lv * BN + j0, v0);
-              if (j0 + 8 < COLS) tmem_ld8(tq + lv * BN + j0 + 8, v1);
-              tmem_ld_wait();
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const long long L = (long long)__float2int_rn(__uint_as_float(v0[j]));
-                acc[j0 + j] += ((L << lsh) + rnd) >> rsh;
-              }
-              if (j0 + 8 < COLS) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                  const long long L = (long long)__float2int_rn(__uint_as_float(v1[j]));
-                  acc[j0 + 8 + j] += ((L << lsh) + rnd) >> rsh;
-                }
-              }
-            }
-          }
-          if (!ok) break;
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&S.tmem_free);
-          ++passc;
-        }
-        // ---- exact conversion, alpha/beta, store (TMEM already free: overlaps the next MMAs).
-        // Each group of 8 columns first loads its 8 old C values and 8 column
-        // exponents, then converts and stores: all loads are in flight together
-        // instead of each one waiting behind the previous column's store.
-        const bool first_pass = c == 0;
-        const bool need_c = !first_pass || !g.sc.beta_zero;
-        for (int j0 = 0; j0 < COLS; j0 += 8) {
-          double cv[8];
-          int fj[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int col = col0 + j0 + j;
-            const bool valid = rvalid && col >= cmin && col < cmax;
-            fj[j] = __ldg(mb + col);
-            cv[j] = (valid && need_c) ? g.C[cbase + (int64_t)(col + coff) * ldcv] : 0.0;
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int col = col0 + j0 + j;
-            const bool valid = rvalid && col >= cmin && col < cmax;
-            const double x = valid ? fixed_to_double(acc[j], Ebase + fj[j]) : 0.0;
-            double* cp = g.C + cbase + (int64_t)(col + coff) * ldcv;
-            if (!g.cplx) {
-              if (valid) {
-                double v = alpha_one ? x : g.sc.alpha_re * x;
-                if (!first_pass) v += cv[j];
-                else if (!g.sc.beta_zero) v = fma(g.sc.beta_re, cv[j], v);
-                *cp = v;
-              }
-            } else {
-              const double xp = __shfl_xor_sync(0xFFFFFFFFu, x, 1);
-              const double cpn = __shfl_xor_sync(0xFFFFFFFFu, cv[j], 1);
-              if (valid) {
-                const double sgn = (rr & 1) ? 1.0 : -1.0;  // im row: +, re row: -
-                double v = fma(g.sc.alpha_re, x, sgn * g.sc.alpha_im * xp);
-                if (!first_pass) v += cv[j];
-                else if (!g.sc.beta_zero)
-                  v = fma(g.sc.beta_re, cv[j], fma(sgn * g.sc.beta_im, cpn, v));
-                *cp = v;
-              }
-            }
-          }
-          // rotate the next 8 accumulators into place (keeps the loop body small)
-#pragma unroll
-          for (int j = 0; j + 8 < COLS; ++j) acc[j] = acc[j + 8];
-        }
-      }
-    }
-  }
-
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                 "r"(kTmemCols));
-  }
-}
-
 // ---- standalone plane cut (exposed for checking the digit arithmetic) ------------------------
 
 __global__ void planes_exp_kernel(int64_t m, int64_t k, const double* X, int64_t ldx, int axis,
@@ -1079,21 +289,6 @@ __global__ void planes_digit_kernel(int64_t m, int64_t k, const double* X, int64
     case 11: { constexpr int S = 11; __VA_ARGS__; }     \
     case 12: { constexpr int S = 12; __VA_ARGS__; }     \
     default: return cudaErrorInvalidValue;              \
-  }
-
-// Same for the GEMM kernel template arguments: the tile width BN (from s)
-// and the compile-time slice count (3, 6 and 9 have unrolled versions).
-#define BG_DISPATCH_GEMM(s, ...)                                           \
-  switch (s) {                                                             \
-    case 3: { constexpr int BNV = 128, SFV = 3; __VA_ARGS__; }             \
-    case 6: { constexpr int BNV = 80, SFV = 6; __VA_ARGS__; }              \
-    case 9: { constexpr int BNV = 48, SFV = 9; __VA_ARGS__; }              \
-    case 1: case 2: case 4: { constexpr int BNV = 128, SFV = 0; __VA_ARGS__; } \
-    case 5: { constexpr int BNV = 96, SFV = 0; __VA_ARGS__; }              \
-    case 7: case 8: { constexpr int BNV = 64, SFV = 0; __VA_ARGS__; }      \
-    case 10: { constexpr int BNV = 48, SFV = 0; __VA_ARGS__; }             \
-    case 11: case 12: { constexpr int BNV = 32, SFV = 0; __VA_ARGS__; }    \
-    default: return cudaErrorInvalidValue;                                 \
   }
 
 }  // namespace
@@ -1397,20 +592,18 @@ static void finish_desc(SplitPlan* p) {
   p->desc = buf;
 }
 
-static cudaError_t set_gemm_attr(int s) {
-  static bool done[kMaxSlices + 1] = {};
+static cudaError_t set_gemm_attr(bg_dtype dt, int s) {
+  static bool done[2][kMaxSlices + 1] = {};
   if (s < 1 || s > kMaxSlices) return cudaErrorInvalidValue;
-  if (done[s]) return cudaSuccess;
-  BG_DISPATCH_GEMM(s, {
-    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<BNV, SFV>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-    if (e == cudaSuccess) done[s] = true;
-    return e;
-  });
+  const int c = dt == BG_C128 ? 1 : 0;
+  if (done[c][s]) return cudaSuccess;
+  cudaError_t e = c ? set_split_gemm_attr_c128(s) : set_split_gemm_attr_r64(s);
+  if (e == cudaSuccess) done[c][s] = true;
+  return e;
 }
 
 static void grids(SplitPlan* p) {
-  set_gemm_attr(p->s);
+  set_gemm_attr(p->dt, p->s);
   p->grid_gemm = (int)std::max<int64_t>(1, std::min<int64_t>(p->sms, p->n_units));
   int bps = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, split_slice_kernel<9, 6>, kSliceThreads, 0);
@@ -1507,11 +700,10 @@ static cudaError_t launch_gemm(SplitPlan* p, void* C, const Scalars& sc, const i
   g.kpass = p->kpass;
   g.a_stages = p->a_stages;
   g.err = d_err;
-  BG_DISPATCH_GEMM(p->s, {
-    split_gemm_kernel<BNV, SFV><<<p->grid_gemm, kGemmThreads, p->smem, st>>>(g);
-    count_launch();
-    return cudaGetLastError();
-  });
+  cudaError_t e = g.cplx ? launch_split_gemm_c128(p->s, p->grid_gemm, p->smem, st, g)
+                         : launch_split_gemm_r64(p->s, p->grid_gemm, p->smem, st, g);
+  count_launch();
+  return e;
 }
 
 bg_status split_plan_run(SplitPlan* p, const void* A, const void* B, void* C, const Scalars& s,

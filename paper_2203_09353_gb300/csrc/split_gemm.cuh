@@ -1,0 +1,376 @@
+// The split-precision tensor-core GEMM kernel (see split.cu for the method),
+// included by the per-type instantiation units.
+#pragma once
+
+#include "split_common.cuh"
+
+namespace bg {
+namespace splitk {
+
+// SF > 0: the slice count is the compile-time constant SF (the MMA issue loop
+// unrolls completely); SF == 0: any slice count g.s with this tile width.
+// CPLX: complex instances (compile-time, so that each version carries only
+// its own epilogue).
+template <int BN, int SF, bool CPLX>
+__global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmArgs g) {
+  constexpr int COLS = BN / 2;  // output columns per epilogue thread
+  constexpr int BTILE = BN * kLineBytes;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  const int s = SF > 0 ? SF : g.s;
+  const int bplanes_bytes = s * BTILE;
+  uint8_t* bbuf = smem;                          // 2 x s B tiles
+  uint8_t* aring = smem + 2 * bplanes_bytes;     // a_stages x 16 KiB
+  GemmBars& S = *reinterpret_cast<GemmBars*>(aring + g.a_stages * kATileBytes);
+  volatile int* abort_flag = &S.abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int NA = g.a_stages;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&S.b_full[i], 1);
+      mbar_init(&S.b_empty[i], 1);
+    }
+    for (int i = 0; i < NA; ++i) {
+      mbar_init(&S.a_full[i], 1);
+      mbar_init(&S.a_empty[i], 1);
+    }
+    for (int i = 0; i < s; ++i) mbar_init(&S.lvl_full[i], 1);
+    mbar_init(&S.tmem_free, kEpiWarps);
+    mbar_init(&S.mma_done, 1);
+    S.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&S.tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = S.tmem_base;
+
+  if (warp == 0) {
+    // ---------------- producer: one TMA bulk copy of the s B planes per k-block, and
+    // the s A planes of the k-block through the A ring
+    if (lane == 0) {
+      uint32_t kbc = 0, afill = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < g.nunits && ok; u += gridDim.x) {
+        const SplitUnit U = g.units[u];
+        int64_t at, bt;
+        int ablk;
+        if (!unit_tiles(g, U, &at, &bt, &ablk)) continue;
+        const int npass = unit_passes(g, U);
+        for (int c = 0; c < npass && ok; ++c) {
+          const int kb_lo = c * g.kpass, kb_hi = min((int)U.nkb, kb_lo + g.kpass);
+          for (int kb = kb_lo; kb < kb_hi && ok; ++kb, ++kbc) {
+            const int buf = kbc & 1;
+            const uint32_t use = kbc >> 1;
+            if (use > 0 && !mbar_wait(&S.b_empty[buf], (use - 1) & 1, abort_flag)) {
+              record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_EMPTY_BARRIER, (int)u);
+              *abort_flag = 1;
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&S.b_full[buf], (uint32_t)bplanes_bytes);
+            bulk_g2s(bbuf + buf * bplanes_bytes, g.tilesB + (bt + (int64_t)kb * s) * BTILE,
+                     (uint32_t)bplanes_bytes, &S.b_full[buf]);
+            for (int p = 0; p < s; ++p, ++afill) {
+              const int slot = afill % NA;
+              const uint32_t ause = afill / NA;
+              if (ause > 0 && !mbar_wait(&S.a_empty[slot], (ause - 1) & 1, abort_flag)) {
+                record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_EMPTY_BARRIER, (int)u);
+                *abort_flag = 1;
+                ok = false;
+                break;
+              }
+              mbar_arrive_expect_tx(&S.a_full[slot], kATileBytes);
+              bulk_g2s(aring + slot * kATileBytes,
+                       g.tilesA + (at + (int64_t)kb * s + p) * kATileBytes, kATileBytes,
+                       &S.a_full[slot]);
+            }
+          }
+        }
+      }
+      // let every copy this thread started land before the CTA can exit
+      for (uint32_t j = kbc > 2 ? kbc - 2 : 0; j < kbc; ++j)
+        mbar_wait_time(&S.b_full[j & 1], (j >> 1) & 1);
+      for (uint32_t j = afill > (uint32_t)NA ? afill - NA : 0; j < afill; ++j)
+        mbar_wait_time(&S.a_full[j % NA], (j / NA) & 1);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: one N-concatenated MMA per A plane and K-step
+    if (lane == 0) {
+      uint32_t kbc = 0, passc = 0;
+      int slot = 0;
+      uint32_t aphase = 0;
+      bool ok = true;
+      const uint32_t bbase = smem_u32(bbuf);
+      const uint32_t abase = smem_u32(aring);
+      for (int64_t u = blockIdx.x; u < g.nunits && ok; u += gridDim.x) {
+        const SplitUnit U = g.units[u];
+        int64_t at_, bt_;
+        int ablk_;
+        if (!unit_tiles(g, U, &at_, &bt_, &ablk_)) continue;
+        const int npass = unit_passes(g, U);
+        for (int c = 0; c < npass && ok; ++c, ++passc) {
+          if (passc > 0 && !mbar_wait(&S.tmem_free, (passc - 1) & 1, abort_flag)) {
+            record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_ACC_EMPTY, (int)u);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int kb_lo = c * g.kpass, kb_hi = min((int)U.nkb, kb_lo + g.kpass);
+          for (int kb = kb_lo; kb < kb_hi && ok; ++kb, ++kbc) {
+            const int buf = kbc & 1;
+            if (!mbar_wait(&S.b_full[buf], (kbc >> 1) & 1, abort_flag)) {
+              record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_FULL_BARRIER, (int)u);
+              *abort_flag = 1;
+              ok = false;
+              break;
+            }
+            const uint64_t bdesc = sw128_desc(bbase + buf * bplanes_bytes);
+            const int nk = (kb == U.nkb - 1) ? U.kmma_last : 4;
+            const bool last_kb = kb == kb_hi - 1;
+            uint32_t acc0 = kb == kb_lo ? 0u : 1u;  // the first MMA of a pass initialises TMEM
+#pragma unroll
+            for (int p = 0; p < (SF > 0 ? SF : kMaxSlices); ++p) {
+              if (SF == 0 && p >= s) break;
+              if (!mbar_wait(&S.a_full[slot], aphase, abort_flag)) {
+                record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_FULL_BARRIER, (int)u);
+                *abort_flag = 1;
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint64_t adesc = sw128_desc(abase + slot * kATileBytes);
+              // B planes 1..s-p (levels p+2 .. s+1) as one N range, cut in pieces of <= 256
+              const int ncat = (s - p) * BN;
+              const int n1 = ncat > 256 ? ncat - 256 : 0;
+              const uint32_t id0 = make_idesc(BM, ncat > 256 ? 256 : ncat);
+              const uint32_t id1 = make_idesc(BM, n1 > 0 ? n1 : 16);
+              const uint32_t d0 = tmem_base + p * BN;
+              constexpr uint64_t kB256 = (256 * kLineBytes) >> 4;
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                if (kk < nk) {
+                  const uint32_t acc = kk == 0 ? acc0 : 1u;
+                  umma_bf16(d0, adesc + 2 * kk, bdesc + 2 * kk, id0, acc);
+                  if (n1 > 0) umma_bf16(d0 + 256, adesc + 2 * kk, bdesc + kB256 + 2 * kk, id1, acc);
+                }
+              }
+              acc0 = 1u;
+              umma_commit(&S.a_empty[slot]);
+              if (last_kb) umma_commit(&S.lvl_full[p]);  // level p+2 is complete
+              if (++slot == NA) {
+                slot = 0;
+                aphase ^= 1;
+              }
+            }
+            if (!ok) break;
+            umma_commit(&S.b_empty[buf]);
+          }
+        }
+      }
+      // all MMAs issued by this thread are complete once mma_done fires
+      umma_commit(&S.mma_done);
+      mbar_wait_time(&S.mma_done, 0);
+    }
+  } else {
+    // ---------------- epilogue: drain levels, recombine, free TMEM, store
+    const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int row = quad * 32 + lane;
+    const int col0 = half * COLS;
+    const uint32_t tq = tmem_base + ((uint32_t)(quad * 32) << 16) + col0;
+    const bool alpha_one = g.sc.alpha_re == 1.0 && g.sc.alpha_im == 0.0;
+    uint32_t passc = 0;
+    bool ok = true;
+    for (int64_t u = blockIdx.x; u < g.nunits && ok; u += gridDim.x) {
+      const SplitUnit U = g.units[u];
+      int64_t at, bt;
+      int ablk;
+      if (!unit_tiles(g, U, &at, &bt, &ablk)) {
+        if (warp == 2 && lane == 0)
+          record_error(g.err, BG_ERR_INVALID_ARG, ERRLOC_CHAIN_INDEX, (int)g.order[U.pos]);
+        continue;
+      }
+      const int32_t* ma = g.metaA + (int64_t)ablk * kMetaStride;
+      const int32_t* mb = g.metaB + (int64_t)U.b_blk * kMetaStride;
+      const int e_i = ma[row];
+      const int F = ma[128 + row] + mb[256] + 1;
+      // output rows/columns of this thread
+      int rr, inst_pos, cmin, cmax, coff;
+      bool rvalid;
+      if (U.g > 1) {
+        const int li = row / U.mrow;
+        rr = row - li * U.mrow;
+        rvalid = li < U.g;
+        inst_pos = U.pos + (rvalid ? li : 0);
+        cmin = li * U.ncol;
+        cmax = cmin + U.ncol;
+        coff = -cmin;
+      } else {
+        rr = U.r0 + row;
+        inst_pos = U.pos;
+        rvalid = true;
+        cmin = 0;
+        cmax = BN;
+        coff = U.c0;
+      }
+      const SInst in = g.inst[g.order[inst_pos]];
+      const int mv = CPLX ? 2 * in.m : in.m;
+      rvalid = rvalid && rr < mv;
+      if (U.g == 1) cmax = min(cmax, in.n - U.c0);
+      const int64_t cbase = (CPLX ? 2 * in.c_off : in.c_off) + rr;
+      const int64_t ldcv = CPLX ? 2 * in.ldc : in.ldc;
+      const int Ebase = F - 62 + e_i - 2 * g.beta;
+      const int npass = unit_passes(g, U);
+      for (int c = 0; c < max(npass, 1) && ok; ++c) {
+        long long acc[COLS];
+#pragma unroll
+        for (int j = 0; j < COLS; ++j) acc[j] = 0;
+        if (npass > 0) {
+#pragma unroll 1
+          for (int lv = 0; lv < s; ++lv) {
+            bool got = true;
+            if (lane == 0) got = mbar_wait(&S.lvl_full[lv], passc & 1, abort_flag);
+            got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
+            if (!got) {
+              if (lane == 0) {
+                record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_ACC_FULL, (int)u);
+                *abort_flag = 1;
+              }
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            int sh = 62 - F - g.beta * lv;
+            sh = max(-63, min(62, sh));
+            const int lsh = sh > 0 ? sh : 0, rsh = sh < 0 ? -sh : 0;
+            const long long rnd = rsh > 0 ? (1ll << (rsh - 1)) : 0ll;
+#pragma unroll
+            for (int j0 = 0; j0 < COLS; j0 += 16) {
+              uint32_t v0[8], v1[8];
+              tmem_ld8(tq + lv * BN + j0, v0);
+              if (j0 + 8 < COLS) tmem_ld8(tq + lv * BN + j0 + 8, v1);
+              tmem_ld_wait();
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const long long L = (long long)__float2int_rn(__uint_as_float(v0[j]));
+                acc[j0 + j] += ((L << lsh) + rnd) >> rsh;
+              }
+              if (j0 + 8 < COLS) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  const long long L = (long long)__float2int_rn(__uint_as_float(v1[j]));
+                  acc[j0 + 8 + j] += ((L << lsh) + rnd) >> rsh;
+                }
+              }
+            }
+          }
+          if (!ok) break;
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&S.tmem_free);
+          ++passc;
+        }
+        // ---- exact conversion, alpha/beta, store (TMEM already free: overlaps the next MMAs).
+        // Each group of 8 columns first loads its 8 old C values and 8 column
+        // exponents, then converts and stores: all loads are in flight together
+        // instead of each one waiting behind the previous column's store.
+        const bool first_pass = c == 0;
+        const bool need_c = !first_pass || !g.sc.beta_zero;
+        for (int j0 = 0; j0 < COLS; j0 += 8) {
+          double cv[8];
+          int fj[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int col = col0 + j0 + j;
+            const bool valid = rvalid && col >= cmin && col < cmax;
+            fj[j] = __ldg(mb + col);
+            cv[j] = (valid && need_c) ? g.C[cbase + (int64_t)(col + coff) * ldcv] : 0.0;
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int col = col0 + j0 + j;
+            const bool valid = rvalid && col >= cmin && col < cmax;
+            const double x = valid ? fixed_to_double(acc[j], Ebase + fj[j]) : 0.0;
+            double* cp = g.C + cbase + (int64_t)(col + coff) * ldcv;
+            if constexpr (!CPLX) {
+              if (valid) {
+                double v = x;
+                if (!alpha_one) v = g.sc.alpha_re * x;
+                if (!first_pass) v += cv[j];
+                else if (!g.sc.beta_zero) v = fma(g.sc.beta_re, cv[j], v);
+                *cp = v;
+              }
+            } else {
+              const double xp = __shfl_xor_sync(0xFFFFFFFFu, x, 1);
+              const double cpn = __shfl_xor_sync(0xFFFFFFFFu, cv[j], 1);
+              if (valid) {
+                const double sgn = (rr & 1) ? 1.0 : -1.0;  // im row: +, re row: -
+                double v = fma(g.sc.alpha_re, x, sgn * g.sc.alpha_im * xp);
+                if (!first_pass) v += cv[j];
+                else if (!g.sc.beta_zero)
+                  v = fma(g.sc.beta_re, cv[j], fma(sgn * g.sc.beta_im, cpn, v));
+                *cp = v;
+              }
+            }
+          }
+          // rotate the next 8 accumulators into place (keeps the loop body small)
+#pragma unroll
+          for (int j = 0; j + 8 < COLS; ++j) acc[j] = acc[j + 8];
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kTmemCols));
+  }
+}
+
+
+// Same for the GEMM kernel template arguments: the tile width BN (from s)
+// and the compile-time slice count (3, 6 and 9 have unrolled versions).
+#define BG_DISPATCH_GEMM(s, ...)                                           \
+  switch (s) {                                                             \
+    case 3: { constexpr int BNV = 128, SFV = 3; __VA_ARGS__; }             \
+    case 6: { constexpr int BNV = 80, SFV = 6; __VA_ARGS__; }              \
+    case 9: { constexpr int BNV = 48, SFV = 9; __VA_ARGS__; }              \
+    case 1: case 2: case 4: { constexpr int BNV = 128, SFV = 0; __VA_ARGS__; } \
+    case 5: { constexpr int BNV = 96, SFV = 0; __VA_ARGS__; }              \
+    case 7: case 8: { constexpr int BNV = 64, SFV = 0; __VA_ARGS__; }      \
+    case 10: { constexpr int BNV = 48, SFV = 0; __VA_ARGS__; }             \
+    case 11: case 12: { constexpr int BNV = 32, SFV = 0; __VA_ARGS__; }    \
+    default: return cudaErrorInvalidValue;                                 \
+  }
+
+template <bool CPLX>
+cudaError_t launch_gemm_t(int s, int grid, size_t smem, cudaStream_t st, const GemmArgs& g) {
+  BG_DISPATCH_GEMM(s, {
+    split_gemm_kernel<BNV, SFV, CPLX><<<grid, kGemmThreads, smem, st>>>(g);
+    return cudaGetLastError();
+  });
+}
+
+template <bool CPLX>
+cudaError_t set_attr_t(int s) {
+  BG_DISPATCH_GEMM(s, {
+    return cudaFuncSetAttribute(split_gemm_kernel<BNV, SFV, CPLX>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  });
+}
+
+}  // namespace splitk
+}  // namespace bg

@@ -244,6 +244,16 @@ def max_over_ranks(pg, v: float) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(pg, v: float) -> float:
+    if pg is None:
+        return v
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
 def run_reference(args, world, rank, pg):
     """--impl reference: the CPU oracle, as it stands, on bounded samples of the workload."""
     if rank != 0:
@@ -295,6 +305,7 @@ def main():
     batch, desc = make_batch(args.config, args.count, rank)
     log(f"generated {desc}")
     flops = batch.flops()
+    job_flops = sum_over_ranks(pg, flops)  # every rank's shard counts toward the job
     A = torch.from_numpy(batch.A).to(dev)
     B = torch.from_numpy(batch.B).to(dev)
     C0 = torch.from_numpy(batch.C).to(dev)
@@ -379,7 +390,7 @@ def main():
         kt, calls = plans[m].kernel_times(reset=True)
         log(f"{m}: {ms:.3f} ms/step")
         res[m] = {"ms_per_step": ms, "steps": steps,
-                  "value": flops * world / (ms * 1e-3) / 1e12,
+                  "value": job_flops / (ms * 1e-3) / 1e12,
                   "kernel_ms": [kt[0] / max(calls, 1), kt[1] / max(calls, 1)]}
         del Cm
 
@@ -447,7 +458,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms = max_over_ranks(pg, e0.elapsed_time(e1) / n2)
-        e2e = {"value": flops * world / (ms * 1e-3) / 1e12, "unit": UNIT,
+        e2e = {"value": job_flops / (ms * 1e-3) / 1e12, "unit": UNIT,
                "h2d_bytes_per_step": int(Ah.nbytes + Bh.nbytes + Ch.nbytes),
                "d2h_bytes_per_step": int(Co.nbytes), "ms_per_step": ms}
         plan.kernel_times(reset=True)

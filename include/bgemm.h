@@ -122,6 +122,40 @@ bg_status batched_gemm_fixed(bg_dtype dtype, int64_t m, int64_t n, int64_t k,
                              void* C, int64_t ldc, int64_t strideC, int64_t batch,
                              const bg_precision* precision, bg_stream_t stream);
 
+/* ---- fixed-size batch without any device allocation -----------------------
+ * No counterpart in the paper: a library service. Same operation, arguments,
+ * layout and checks as batched_gemm_fixed, split mode only (precision->mode
+ * must be BG_MODE_SPLIT_BF16, else BG_ERR_INVALID_ARG). It is meant for
+ * callers that must not allocate device memory while they run: a process
+ * whose device memory is already handed out to another allocator (a caching
+ * allocator holding the whole GPU), or a latency-critical loop in which a
+ * cudaMalloc/cudaFree would stall or synchronise the device.
+ *  - Workspace: every buffer the split path needs (digit tiles, line
+ *    exponents, work tables, the device error word) is laid out inside one
+ *    static device array of 64 MiB per device (67108864 bytes), part of the
+ *    library image. Nothing is allocated or freed, by this library or any
+ *    other, on any call. A batch whose workspace does not fit is rejected
+ *    with BG_ERR_INVALID_ARG before any work is queued, the message giving
+ *    the bytes it needs.
+ *  - Set-up: the first call on each device looks up the array's address on
+ *    that device (the CUDA runtime loads the module holding it then). Make
+ *    that first call before any stream capture.
+ *  - Each call clears what must start at zero (error word, exponent stores)
+ *    and uploads its work tables from host memory on `stream`.
+ *  - Concurrency: all calls on one device share the one array. Calls queued
+ *    on the same stream are ordered and safe; calls whose work overlaps in
+ *    time (other streams, other host threads) race on the array and give
+ *    wrong results.
+ *  - A device-side wait that runs out of time (see bg_check_device_errors)
+ *    leaves its code only in the array's error word, which the next call
+ *    clears; this entry point does not read it back. */
+bg_status batched_gemm_fixed_static(bg_dtype dtype, int64_t m, int64_t n, int64_t k,
+                                    const void* alpha, const void* A, int64_t lda,
+                                    int64_t strideA, const void* B, int64_t ldb, int64_t strideB,
+                                    const void* beta, void* C, int64_t ldc, int64_t strideC,
+                                    int64_t batch, const bg_precision* precision,
+                                    bg_stream_t stream);
+
 /* ---- Eq. (1), variable-size batch: plan -----------------------------------
  * Sec. 2 (variable-size batches, per-size tiling strategies): builds the
  * schedule for `count` instances described by the HOST array `host_table`

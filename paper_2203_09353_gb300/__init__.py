@@ -33,7 +33,7 @@ STATUS = {0: "BG_OK", 1: "BG_ERR_INVALID_ARG", 2: "BG_ERR_UNSUPPORTED", 3: "BG_E
           4: "BG_ERR_NOMEM", 5: "BG_ERR_CAPTURE", 6: "BG_ERR_TIMEOUT"}
 
 # Every symbol include/bgemm.h declares (the loader checks they are all exported).
-EXPORTS = ("batched_gemm_fixed", "batched_gemm_plan", "batched_gemm_grouped", "chain_plan",
+EXPORTS = ("batched_gemm_fixed", "batched_gemm_fixed_static", "batched_gemm_plan", "batched_gemm_grouped", "chain_plan",
            "chain_step", "bg_plan_destroy", "bg_plan_get_info", "bg_plan_describe",
            "bg_plan_kernel_times", "bg_rel_err",
            "bg_unitarity_drift", "bg_split_planes", "bg_check_device_errors",
@@ -77,6 +77,8 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     sig = {
         "batched_gemm_fixed": [i32, i64, i64, i64, vp, vp, i64, i64, vp, i64, i64, vp, vp, i64,
                                i64, i64, P(Precision), vp],
+        "batched_gemm_fixed_static": [i32, i64, i64, i64, vp, vp, i64, i64, vp, i64, i64, vp, vp,
+                                      i64, i64, i64, P(Precision), vp],
         "batched_gemm_plan": [P(vp), i32, i64, P(Instance), P(Precision), u32, ctypes.c_char_p,
                               vp],
         "batched_gemm_grouped": [vp, vp, vp, vp, vp, vp, vp],
@@ -189,6 +191,21 @@ def batched_gemm_fixed(dtype, m, n, k, alpha, A, lda, strideA, B, ldb, strideB, 
                                   ldb, strideB, _scalar(dt, beta), _ptr(C), ldc, strideC, batch,
                                   ctypes.byref(prec) if prec is not None else None,
                                   _stream(stream)))
+
+
+def batched_gemm_fixed_static(dtype, m, n, k, alpha, A, lda, strideA, B, ldb, strideB, beta, C,
+                              ldc, strideC, batch, prec: Precision, stream=None) -> None:
+    """The split-mode fixed-size batch with its whole workspace in the library's static
+    64 MiB device array: allocates no device memory, for callers that must not (C ABI
+    batched_gemm_fixed_static). Calls that overlap in time on one device race on that
+    array; calls queued on one stream are safe."""
+    lib = load_library()
+    dt = dtype_code(dtype)
+    _check(lib.batched_gemm_fixed_static(dt, m, n, k, _scalar(dt, alpha), _ptr(A), lda, strideA,
+                                         _ptr(B), ldb, strideB, _scalar(dt, beta), _ptr(C), ldc,
+                                         strideC, batch,
+                                         ctypes.byref(prec) if prec is not None else None,
+                                         _stream(stream)))
 
 
 def _instances(table) -> ctypes.Array:

@@ -612,15 +612,17 @@ void assign_classes(bg_plan* p) {
 
 extern "C" {
 
-bg_status batched_gemm_fixed(bg_dtype dtype, int64_t m, int64_t n, int64_t k, const void* alpha,
+// Checks shared by the two fixed-size entry points. Sets *nothing_to_do for an
+// empty batch (m, n or batch zero), which both treat as a no-op.
+static bg_status check_fixed(bg_dtype dtype, int64_t m, int64_t n, int64_t k, const void* alpha,
                              const void* A, int64_t lda, int64_t strideA, const void* B,
                              int64_t ldb, int64_t strideB, const void* beta, void* C, int64_t ldc,
                              int64_t strideC, int64_t batch, const bg_precision* precision,
-                             bg_stream_t stream) {
+                             bg_precision* pr, Scalars* sc, bool* nothing_to_do) {
+  *nothing_to_do = false;
   bg_status s = check_dtype(dtype);
   if (s != BG_OK) return s;
-  bg_precision pr;
-  if ((s = check_precision(precision, &pr)) != BG_OK) return s;
+  if ((s = check_precision(precision, pr)) != BG_OK) return s;
   if (m < 0 || n < 0 || k < 0 || batch < 0)
     return fail(BG_ERR_INVALID_ARG, "negative size (m=%lld n=%lld k=%lld batch=%lld)",
                 (long long)m, (long long)n, (long long)k, (long long)batch);
@@ -631,16 +633,33 @@ bg_status batched_gemm_fixed(bg_dtype dtype, int64_t m, int64_t n, int64_t k, co
     return fail(BG_ERR_INVALID_ARG, "leading dimension below the row count");
   if (strideA < 0 || strideB < 0 || strideC < 0)
     return fail(BG_ERR_INVALID_ARG, "negative stride");
-  if (batch == 0 || m == 0 || n == 0) return BG_OK;
+  if (batch == 0 || m == 0 || n == 0) {
+    *nothing_to_do = true;
+    return BG_OK;
+  }
   if (!alpha || !beta) return fail(BG_ERR_INVALID_ARG, "alpha and beta must be host pointers");
-  const Scalars sc = make_scalars(dtype, alpha, beta);
-  if (!C || (!sc.alpha_zero && k > 0 && (!A || !B)))
+  *sc = make_scalars(dtype, alpha, beta);
+  if (!C || (!sc->alpha_zero && k > 0 && (!A || !B)))
     return fail(BG_ERR_INVALID_ARG, "null matrix pointer");
   if (!aligned(C, dtype) || (A && !aligned(A, dtype)) || (B && !aligned(B, dtype)))
     return fail(BG_ERR_INVALID_ARG, "matrix pointer not %d-byte aligned", dtype == BG_C128 ? 16 : 8);
   if (strideC > 0 && strideC < ldc * (n - 1) + m && batch > 1)
     return fail(BG_ERR_INVALID_ARG, "strideC makes C instances overlap");
   if (fault_injected()) return fail(BG_ERR_CUDA, "injected launch fault (BGEMM_FAULT=launch)");
+  return BG_OK;
+}
+
+bg_status batched_gemm_fixed(bg_dtype dtype, int64_t m, int64_t n, int64_t k, const void* alpha,
+                             const void* A, int64_t lda, int64_t strideA, const void* B,
+                             int64_t ldb, int64_t strideB, const void* beta, void* C, int64_t ldc,
+                             int64_t strideC, int64_t batch, const bg_precision* precision,
+                             bg_stream_t stream) {
+  bg_precision pr;
+  Scalars sc;
+  bool empty = false;
+  bg_status s = check_fixed(dtype, m, n, k, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc,
+                            strideC, batch, precision, &pr, &sc, &empty);
+  if (s != BG_OK || empty) return s;
   DeviceCtx* ctx;
   if ((s = get_ctx(&ctx)) != BG_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -655,6 +674,34 @@ bg_status batched_gemm_fixed(bg_dtype dtype, int64_t m, int64_t n, int64_t k, co
   return split_fixed(dtype, pr, m, n, k, sc, A, lda, strideA, B, ldb, strideB, C, ldc, strideC,
                      batch, &ctx->ws, ctx->sms, ctx->d_err, stream_capturing(st), st,
                      &g_last_error);
+}
+
+bg_status batched_gemm_fixed_static(bg_dtype dtype, int64_t m, int64_t n, int64_t k,
+                                    const void* alpha, const void* A, int64_t lda,
+                                    int64_t strideA, const void* B, int64_t ldb, int64_t strideB,
+                                    const void* beta, void* C, int64_t ldc, int64_t strideC,
+                                    int64_t batch, const bg_precision* precision,
+                                    bg_stream_t stream) {
+  bg_precision pr;
+  Scalars sc;
+  bool empty = false;
+  bg_status s = check_fixed(dtype, m, n, k, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc,
+                            strideC, batch, precision, &pr, &sc, &empty);
+  if (s != BG_OK) return s;
+  if (pr.mode != BG_MODE_SPLIT_BF16)
+    return fail(BG_ERR_INVALID_ARG,
+                "batched_gemm_fixed_static runs the split mode only (precision.mode must be "
+                "BG_MODE_SPLIT_BF16)");
+  if (empty) return BG_OK;
+  int dev = 0, sms = 0;
+  BG_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  BG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  void* scratch = nullptr;
+  size_t bytes = 0;
+  if ((s = static_scratch(&scratch, &bytes, &g_last_error)) != BG_OK) return s;
+  return split_fixed_in_scratch(dtype, pr, m, n, k, sc, A, lda, strideA, B, ldb, strideB, C, ldc,
+                                strideC, batch, scratch, bytes, sms,
+                                reinterpret_cast<cudaStream_t>(stream), &g_last_error);
 }
 
 bg_status batched_gemm_plan(bg_plan** out, bg_dtype dtype, int64_t count,

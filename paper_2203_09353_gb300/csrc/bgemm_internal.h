@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "bgemm.h"
 
 namespace bg {
@@ -101,5 +103,11 @@ enum DevErrLoc : int {
 
 // Host bookkeeping.
 void count_launch(int n = 1);
+
+// ---- static scratch (noalloc.cu) ----
+// Capacity of the per-device static scratch array, in bytes.
+size_t static_scratch_capacity();
+// Address of the static scratch on the current device (looked up once per device).
+bg_status static_scratch(void** out, size_t* bytes, std::string* err);
 
 }  // namespace bg

@@ -443,9 +443,19 @@ static int kmma_last_of(int kv) {
   return (rem + 15) / 16;
 }
 
-// Builds jobs and units for instances (non-chain plans).
-static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& table,
-                                 std::string* err) {
+// Host-side schedule of a (non-chain) split plan: instances, order list,
+// slice jobs, GEMM units and the sizes of the tile and meta stores.
+struct HostTables {
+  std::vector<SInst> inst;
+  std::vector<int32_t> order;
+  std::vector<SliceJob> jobs;
+  std::vector<SplitUnit> units;
+  int64_t tileA = 0, tileB = 0, n_jobs_A = 0;
+  int32_t blkA = 0, blkB = 0;
+};
+
+static void make_tables(const SplitPlan* p, const std::vector<bg_instance>& table,
+                        HostTables* out) {
   const bool cplx = p->dt == BG_C128;
   const int s = p->s, BN = p->bn;
   std::vector<SInst> inst(table.size());
@@ -555,16 +565,35 @@ static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& t
     if (ia < jobsA.size()) jobs.push_back(jobsA[ia++]);
     if (ib < jobsB.size()) jobs.push_back(jobsB[ib++]);
   }
-  p->n_jobs = (int64_t)jobs.size();
-  p->n_jobs_A = (int64_t)jobsA.size();
-  p->n_units = (int64_t)units.size();
+  out->inst = std::move(inst);
+  out->order = std::move(order);
+  out->jobs = std::move(jobs);
+  out->units = std::move(units);
+  out->tileA = tileA;
+  out->tileB = tileB;
+  out->blkA = blkA;
+  out->blkB = blkB;
+  out->n_jobs_A = (int64_t)jobsA.size();
+}
+
+// Builds jobs and units for instances (non-chain plans) and allocates the
+// plan's device tables and workspace.
+static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& table,
+                                 std::string* err) {
+  HostTables t;
+  make_tables(p, table, &t);
+  const int64_t tileA = t.tileA, tileB = t.tileB;
+  const int32_t blkA = t.blkA, blkB = t.blkB;
+  p->n_jobs = (int64_t)t.jobs.size();
+  p->n_jobs_A = t.n_jobs_A;
+  p->n_units = (int64_t)t.units.size();
   p->count = (int64_t)table.size();
-  const size_t btile = (size_t)BN * kLineBytes;
+  const size_t btile = (size_t)p->bn * kLineBytes;
   cudaError_t e;
-  if ((e = dput(&p->d_jobs, jobs, &p->bytes)) != cudaSuccess ||
-      (e = dput(&p->d_units, units, &p->bytes)) != cudaSuccess ||
-      (e = dput(&p->d_inst, inst, &p->bytes)) != cudaSuccess ||
-      (e = dput(&p->d_order, order, &p->bytes)) != cudaSuccess ||
+  if ((e = dput(&p->d_jobs, t.jobs, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_units, t.units, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_inst, t.inst, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_order, t.order, &p->bytes)) != cudaSuccess ||
       (e = dalloc(reinterpret_cast<void**>(&p->tilesA), (size_t)tileA * kATileBytes, &p->bytes)) !=
           cudaSuccess ||
       (e = dalloc(reinterpret_cast<void**>(&p->tilesB), (size_t)tileB * btile, &p->bytes)) !=
@@ -757,6 +786,76 @@ bg_status split_fixed(bg_dtype dt, const bg_precision& pr, int64_t m, int64_t n,
     }
   }
   return split_plan_run(p, A, B, C, s, d_err, st, err);
+}
+
+// ---- fixed-size split batch in caller-provided device scratch ---------------------------------
+
+// Lays the whole split plan (error word, meta stores, tables, digit tiles) out
+// in `scratch` (device memory of the current device, `scratch_bytes` long,
+// 256-byte aligned) and runs it. Allocates no device memory; fails with
+// BG_ERR_INVALID_ARG when the plan does not fit.
+bg_status split_fixed_in_scratch(bg_dtype dt, const bg_precision& pr, int64_t m, int64_t n,
+                                 int64_t k, const Scalars& sc, const void* A, int64_t lda,
+                                 int64_t sA, const void* B, int64_t ldb, int64_t sB, void* C,
+                                 int64_t ldc, int64_t sC, int64_t batch, void* scratch,
+                                 size_t scratch_bytes, int sms, cudaStream_t st,
+                                 std::string* err) {
+  SplitPlan p;  // host object only: every device pointer below points into `scratch`
+  if (!setup_common(&p, dt, pr, sms, err)) return BG_ERR_INVALID_ARG;
+  std::vector<bg_instance> table((size_t)batch);
+  for (int64_t i = 0; i < batch; ++i)
+    table[i] = bg_instance{m, n, k, lda, ldb, ldc, i * sA, i * sB, i * sC};
+  HostTables t;
+  make_tables(&p, table, &t);
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t meta_a = (size_t)std::max(t.blkA, 1) * kMetaStride * 4;
+  const size_t meta_b = (size_t)std::max(t.blkB, 1) * kMetaStride * 4;
+  size_t off = 0;
+  const size_t o_err = off;    off += up(4 * sizeof(int));
+  const size_t o_ma = off;     off += up(meta_a);
+  const size_t o_mb = off;     off += up(meta_b);
+  const size_t o_jobs = off;   off += up(t.jobs.size() * sizeof(SliceJob) + 1);
+  const size_t o_units = off;  off += up(t.units.size() * sizeof(SplitUnit) + 1);
+  const size_t o_inst = off;   off += up(t.inst.size() * sizeof(SInst) + 1);
+  const size_t o_order = off;  off += up(t.order.size() * sizeof(int32_t) + 1);
+  const size_t o_ta = off;     off += up((size_t)t.tileA * kATileBytes);
+  const size_t o_tb = off;     off += up((size_t)t.tileB * p.bn * kLineBytes);
+  if (off > scratch_bytes) {
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "problem needs %zu bytes of split workspace; the static scratch holds %zu",
+             off, scratch_bytes);
+    return set_err(err, BG_ERR_INVALID_ARG, buf);
+  }
+  uint8_t* base = static_cast<uint8_t*>(scratch);
+  int* d_err = reinterpret_cast<int*>(base + o_err);
+  p.metaA = reinterpret_cast<int32_t*>(base + o_ma);
+  p.metaB = reinterpret_cast<int32_t*>(base + o_mb);
+  p.d_jobs = reinterpret_cast<SliceJob*>(base + o_jobs);
+  p.d_units = reinterpret_cast<SplitUnit*>(base + o_units);
+  p.d_inst = reinterpret_cast<SInst*>(base + o_inst);
+  p.d_order = reinterpret_cast<int32_t*>(base + o_order);
+  p.tilesA = base + o_ta;
+  p.tilesB = base + o_tb;
+  p.n_jobs = (int64_t)t.jobs.size();
+  p.n_jobs_A = t.n_jobs_A;
+  p.n_units = (int64_t)t.units.size();
+  p.count = batch;
+  cudaError_t e;
+  // the scratch keeps the previous call's contents: clear the error word and the meta stores
+  if ((e = cudaMemsetAsync(base, 0, o_jobs, st)) != cudaSuccess)
+    return cuda_err(err, e, "static scratch clear");
+  struct Piece { size_t off; const void* src; size_t bytes; };
+  const Piece pieces[] = {{o_jobs, t.jobs.data(), t.jobs.size() * sizeof(SliceJob)},
+                          {o_units, t.units.data(), t.units.size() * sizeof(SplitUnit)},
+                          {o_inst, t.inst.data(), t.inst.size() * sizeof(SInst)},
+                          {o_order, t.order.data(), t.order.size() * sizeof(int32_t)}};
+  for (const Piece& pc : pieces)
+    if (pc.bytes && (e = cudaMemcpyAsync(base + pc.off, pc.src, pc.bytes, cudaMemcpyHostToDevice,
+                                         st)) != cudaSuccess)
+      return cuda_err(err, e, "static scratch table upload");
+  grids(&p);
+  return split_plan_run(&p, A, B, C, sc, d_err, st, err);
 }
 
 // ---- chain plans -----------------------------------------------------------------------------

@@ -52,6 +52,15 @@ bg_status split_fixed(bg_dtype dt, const bg_precision& pr, int64_t m, int64_t n,
                       SplitWorkspace* ws, int sms, int* d_err, bool capturing, cudaStream_t st,
                       std::string* err);
 
+// Runs a fixed-size split batch with every workspace inside `scratch`
+// (device memory, 256-byte aligned, scratch_bytes long); allocates nothing.
+bg_status split_fixed_in_scratch(bg_dtype dt, const bg_precision& pr, int64_t m, int64_t n,
+                                 int64_t k, const Scalars& s, const void* A, int64_t lda,
+                                 int64_t sA, const void* B, int64_t ldb, int64_t sB, void* C,
+                                 int64_t ldc, int64_t sC, int64_t batch, void* scratch,
+                                 size_t scratch_bytes, int sms, cudaStream_t st,
+                                 std::string* err);
+
 bg_status split_chain_prepare_pool(SplitPlan* p, const void* U, int* d_err, cudaStream_t st,
                                    std::string* err);
 bg_status split_chain_step(SplitPlan* p, const void* U, const int32_t* idx_row, const void* Cin,

@@ -35,6 +35,25 @@ METRIC = "batched GEMM TFLOP/s & roofline %: FP64 vs split-BF16 at same error"
 UNIT = "TFLOP/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one
+# ncu capture of the 2000-instance log-uniform size-mix batch, seed 3 (profiles/),
+# divided by that batch's algorithmic bytes (990601216): a full launch's traffic
+# is this ratio times its own algorithmic bytes. Valid only while the split kernel sources
+# hash to NCU_SOURCES_SHA; otherwise the traffic is reported as null.
+NCU_TRAFFIC_PER_BYTE = {"split9": {"gemm": 1.806018e9 / 990601216.0,
+                                   "slicer": 2.143558e9 / 990601216.0}}
+NCU_SOURCES = ("split.cu", "split_common.cuh", "split_gemm.cuh", "split_gemm_r64.cu")
+NCU_SOURCES_SHA = "39a0f18a75716269"
+
+
+def split_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in NCU_SOURCES:
+        with open(os.path.join(ROOT, "paper_2203_09353_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def parse_args():
     p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
@@ -121,7 +140,7 @@ def oracle_on(batch, ids):
 
 def calibrated_sample(batch, seconds: float):
     """Oracle sample sized to take about `seconds` on this host's cores."""
-    ids = sample_ids(batch, 0.002)
+    ids = sample_ids(batch, 0.01)
     _, dt, fl, _ = oracle_on(batch, ids)
     rate = fl / max(dt, 1e-6)
     frac = min(1.0, seconds * rate / (2.0 * batch.table[:, 0].astype(np.float64)
@@ -395,6 +414,7 @@ def main():
         del Cm
 
     # --- roofline of the dominant kernel of each mode
+    traffic_ok = args.config == 4 and split_sources_sha() == NCU_SOURCES_SHA
     t = batch.table.astype(np.float64)
     esz = 16.0 if batch.dtype == "c128" else 8.0
     ab_elems = float(np.sum(t[:, 0] * t[:, 2] + t[:, 2] * t[:, 1]))
@@ -416,7 +436,9 @@ def main():
             pk_bf16 = pk["bf16_tflops"]
             r["roofline"] = {"kernel": "split_gemm_kernel (tcgen05)", "bound": "tensor",
                              "achieved": ach, "peak": pk_bf16, "unit": "TFLOP/s",
-                             "frac": ach / pk_bf16, "traffic": None,
+                             "frac": ach / pk_bf16,
+                             "traffic": (NCU_TRAFFIC_PER_BYTE[m]["gemm"] * batch.bytes_moved()
+                                         if traffic_ok and m in NCU_TRAFFIC_PER_BYTE else None),
                              "peak_source": f"bf16 burst, {pk_src} (MEASURED_PEAKS.json)"}
             sl_ms = r["kernel_ms"][0]
             sl_bytes = ab_elems * (esz + 2.0 * s * (4.0 if batch.dtype == "c128" else 1.0))
@@ -424,7 +446,9 @@ def main():
                            "achieved": sl_bytes / (sl_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
                            "unit": "GB/s",
                            "frac": sl_bytes / (sl_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
-                           "ms": sl_ms}
+                           "ms": sl_ms, "algorithmic_bytes": sl_bytes,
+                           "traffic": (NCU_TRAFFIC_PER_BYTE[m]["slicer"] * batch.bytes_moved()
+                                       if traffic_ok and m in NCU_TRAFFIC_PER_BYTE else None)}
             r["tensor_tflops_per_step"] = tf / (r["ms_per_step"] * 1e-3) / 1e12
         r["error"] = errs.get(m, {})
 

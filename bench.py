@@ -140,7 +140,7 @@ def oracle_on(batch, ids):
 
 def calibrated_sample(batch, seconds: float):
     """Oracle sample sized to take about `seconds` on this host's cores."""
-    ids = sample_ids(batch, 0.01)
+    ids = sample_ids(batch, 0.05)
     _, dt, fl, _ = oracle_on(batch, ids)
     rate = fl / max(dt, 1e-6)
     frac = min(1.0, seconds * rate / (2.0 * batch.table[:, 0].astype(np.float64)

@@ -121,7 +121,6 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
   __shared__ unsigned long long s_max[128];
   __shared__ unsigned long long s_n2[128];  // sum of alpha^2 in units of 2^-8 (rounded up)
   __shared__ int s_e[128];
-  __shared__ int s_R[128];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int cc = lane & 7;        // chunk of 8 k values inside a 64-wide k-block
   const int lsub = lane >> 3;     // line within the warp's group of 4
@@ -131,7 +130,7 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
     const bool isA = J.side == 0;
     const int kv = J.kv;
     const int lines = isA ? BM : a.bn;
-    const int groups = lines / 4;
+    const int groups = J.nl / 4;  // the job's lines [l0, l0 + nl) in groups of 4
     const int items = groups * J.nkb;
     const int tile_bytes = lines * kLineBytes;
     uint8_t* tiles = isA ? a.tilesA : a.tilesB;
@@ -142,7 +141,7 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
     __syncthreads();
     // ---- phase 1: line maxima (exponents)
     for (int wi = warp; wi < items; wi += kWarps) {
-      const int l = (wi % groups) * 4 + lsub, kb = wi / groups;
+      const int l = J.l0 + (wi % groups) * 4 + lsub, kb = wi / groups;
       const int li = l / J.span;
       const int line = J.org + l % J.span;
       SInst in{};
@@ -171,7 +170,7 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
     __syncthreads();
     // ---- phase 2: digit planes and the norm of the absolute digit weights
     for (int wi = warp; wi < items; wi += kWarps) {
-      const int l = (wi % groups) * 4 + lsub, kb = wi / groups;
+      const int l = J.l0 + (wi % groups) * 4 + lsub, kb = wi / groups;
       const int li = l / J.span;
       const int line = J.org + l % J.span;
       SInst in{};
@@ -218,21 +217,11 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
       if (cc == 0 && n2) atomicAdd(&s_n2[l], (unsigned long long)n2);
     }
     __syncthreads();
-    // ---- phase 3: meta (exponent, norm exponent, block max of the norm exponent)
+    // ---- phase 3: meta of the job's lines (exponent, norm exponent)
     int32_t* meta = (isA ? a.metaA : a.metaB) + (int64_t)J.blk * kMetaStride;
-    if (t < 128) {
-      const int R = t < lines ? norm_exponent((float)s_n2[t] * (1.0f / 256.0f)) : -126;
-      s_R[t] = R;
+    if (t >= J.l0 && t < J.l0 + J.nl) {
       meta[t] = s_e[t];
-      meta[128 + t] = R;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      int mx = -126;
-      for (int l = lane; l < 128; l += 32) mx = max(mx, s_R[l]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
-      if (lane == 0) meta[256] = mx;
+      meta[128 + t] = norm_exponent((float)s_n2[t] * (1.0f / 256.0f));
     }
     __syncthreads();
   }
@@ -443,6 +432,28 @@ static int kmma_last_of(int kv) {
   return (rem + 15) / 16;
 }
 
+// Cuts a block job whose FP64 values exceed kSliceJobBytes into jobs of
+// fewer lines (halving while the count stays a multiple of 4). The slicer
+// reads a job's values twice (line maxima, then digits); smaller jobs keep
+// what all resident CTAs read between the two passes within L2.
+static void split_jobs(std::vector<SliceJob>* jobs, int bn) {
+  std::vector<SliceJob> out;
+  out.reserve(jobs->size() * 2);
+  for (const SliceJob& j : *jobs) {
+    const int lines = j.side == 0 ? BM : bn;
+    const int64_t line_bytes = (int64_t)j.nkb * BK * 8;
+    int nl = lines;
+    while (nl * line_bytes > kSliceJobBytes && nl % 2 == 0 && (nl / 2) % 4 == 0) nl /= 2;
+    for (int l0 = 0; l0 < lines; l0 += nl) {
+      SliceJob sj = j;
+      sj.l0 = (int16_t)l0;
+      sj.nl = (int16_t)nl;
+      out.push_back(sj);
+    }
+  }
+  jobs->swap(out);
+}
+
 // Host-side schedule of a (non-chain) split plan: instances, order list,
 // slice jobs, GEMM units and the sizes of the tile and meta stores.
 struct HostTables {
@@ -565,6 +576,7 @@ static void make_tables(const SplitPlan* p, const std::vector<bg_instance>& tabl
     if (ia < jobsA.size()) jobs.push_back(jobsA[ia++]);
     if (ib < jobsB.size()) jobs.push_back(jobsB[ib++]);
   }
+  split_jobs(&jobs, BN);
   out->inst = std::move(inst);
   out->order = std::move(order);
   out->jobs = std::move(jobs);
@@ -943,7 +955,10 @@ bg_status split_chain_create(SplitPlan** out, bg_dtype dt, const bg_precision& p
   }
   std::stable_sort(units.begin(), units.end(),
                    [](const SplitUnit& a, const SplitUnit& b) { return a.nkb > b.nkb; });
-  std::vector<SliceJob> jobs = jobsA;  // pool jobs first, then walker jobs
+  // pool jobs first, then walker jobs (the chain step slices the two parts separately)
+  split_jobs(&jobsA, BN);
+  split_jobs(&jobsB, BN);
+  std::vector<SliceJob> jobs = jobsA;
   jobs.insert(jobs.end(), jobsB.begin(), jobsB.end());
   p->n_jobs = (int64_t)jobs.size();
   p->n_jobs_A = (int64_t)jobsA.size();

@@ -18,17 +18,25 @@ constexpr int kLineBytes = BK * 2;        // 128 bytes: one row of a tile
 constexpr int kMaxAStages = 8;
 constexpr int kGemmThreads = 320;
 constexpr int kEpiWarps = 8;
-constexpr int kMetaStride = 264;  // int32 per block: e[128], R[128], max R at [256]
+constexpr int kMetaStride = 264;  // int32 per block: e[128], R[128] (then padding)
 constexpr int kTmemCols = 512;
 constexpr int kSliceThreads = 256;
+// Largest FP64 footprint of one slicer job (see split_jobs).
+constexpr int64_t kSliceJobBytes = 131072;
 constexpr int kMaxDynSmem = 232448;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any single wait
 
 // Tile width (columns of the output tile, rows of a B tile) for s planes:
 // the largest multiple of 16 (at most 128) with s * BN <= 512 TMEM columns.
+// Output tile width of the split GEMM for s slices. Up to 5 slices the tile's
+// s level accumulators fit TMEM twice (2 s BN <= 512 columns): the MMAs of the
+// next tile then run while the epilogue empties the other copy. From 6
+// slices on one copy fills TMEM and the epilogue empties it level by level
+// (a double-buffered 6-slice tile would be 32 wide, which measured slower).
 __host__ __device__ constexpr int bn_for(int s) {
-  return s <= 4 ? 128 : s == 5 ? 96 : s == 6 ? 80 : s <= 8 ? 64 : s <= 10 ? 48 : 32;
+  return s <= 2 ? 128 : s <= 4 ? 64 : s == 5 ? 48 : s == 6 ? 80 : s <= 8 ? 64 : s <= 10 ? 48 : 32;
 }
+__host__ __device__ constexpr bool double_buffered(int s) { return s <= 5; }
 
 struct SInst {
   int64_t a_off, b_off, c_off;  // user element offsets
@@ -47,6 +55,8 @@ struct SliceJob {
   int16_t nkb;    // k-blocks of 64
   int32_t org;    // first line of the block within its instance (big instances)
   int32_t kv;     // virtual k' of the instances
+  int16_t l0;     // first line of the block this job cuts
+  int16_t nl;     // lines this job cuts (a multiple of 4)
 };
 
 struct SplitUnit {
@@ -412,6 +422,8 @@ struct GemmBars {
   uint64_t a_full[kMaxAStages];
   uint64_t a_empty[kMaxAStages];
   uint64_t lvl_full[kMaxSlices];
+  uint64_t acc_full[2];   // double-buffered TMEM: accumulator copy b holds a finished tile
+  uint64_t acc_empty[2];  // double-buffered TMEM: the epilogue has emptied copy b
   uint64_t tmem_free;
   uint64_t mma_done;
   uint32_t tmem_base;
@@ -481,6 +493,28 @@ __device__ __forceinline__ double fixed_to_double(long long a, int E) {
   return fixed_to_double_slow(sign, mant, ex);
 }
 
+// Branch-free form of fixed_to_double for the normal range, so that a group
+// of conversions compiles to straight-line code the scheduler can interleave.
+// Sets `bad` when the result is not a normal FP64 number (or a == 0 is not
+// the case and the exponent is out of range); the caller then redoes that
+// element with fixed_to_double. a == 0 gives 0.0 without setting `bad`.
+__device__ __forceinline__ double fixed_to_double_fast(long long a, int E, bool& bad) {
+  const unsigned long long sign = (unsigned long long)a & (1ull << 63);
+  const unsigned long long u = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+  const int lz = __clzll((long long)u);  // 64 for u == 0
+  const unsigned long long un = u << (lz & 63);
+  unsigned long long mant = un >> 11;
+  const unsigned long long rem = un & 0x7FFull;
+  mant += (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
+  const unsigned long long carry = mant >> 53;  // rounding overflowed into bit 53
+  mant >>= carry;
+  const int biased = 63 - lz + E + 1023 + (int)carry;
+  const bool zero = u == 0;
+  bad = bad || (!zero && (biased < 1 || biased > 2046));
+  const unsigned long long bits =
+      sign | ((unsigned long long)(biased & 0x7FF) << 52) | (mant & ((1ull << 52) - 1));
+  return zero ? 0.0 : __longlong_as_double((long long)bits);
+}
 
 // GEMM launchers, one per element type (split_gemm_r64.cu, split_gemm_c128.cu).
 cudaError_t launch_split_gemm_r64(int s, int grid, size_t smem, cudaStream_t st, const GemmArgs& g);

@@ -7,13 +7,80 @@
 namespace bg {
 namespace splitk {
 
+// Final stage of the epilogue for 8 columns of one row: exact conversion of
+// the fixed-point sums, alpha and beta of Eq. (1), store. The 8 old C values
+// and column exponents are loaded first, so that all loads are in flight
+// together; the conversions are straight-line code and the rare value
+// outside the normal FP64 range is redone exactly afterwards.
+template <bool CPLX, bool FASTCONV>
+__device__ __forceinline__ void epi_store8(const GemmArgs& g, const long long (&acc)[8],
+                                           const int32_t* mb, int colb, bool rvalid, int cmin,
+                                           int cmax, int coff, int64_t cbase, int64_t ldcv,
+                                           int Ebase, bool first_pass, bool alpha_one, int rr) {
+  const bool need_c = !first_pass || !g.sc.beta_zero;
+  double cv[8];
+  int fj[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int col = colb + j;
+    const bool valid = rvalid && col >= cmin && col < cmax;
+    fj[j] = __ldg(mb + col);
+    cv[j] = (valid && need_c) ? g.C[cbase + (int64_t)(col + coff) * ldcv] : 0.0;
+  }
+  double xs[8];
+  if constexpr (FASTCONV) {
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) xs[j] = fixed_to_double_fast(acc[j], Ebase + fj[j], bad);
+    if (__builtin_expect(bad, 0)) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) xs[j] = fixed_to_double(acc[j], Ebase + fj[j]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) xs[j] = fixed_to_double(acc[j], Ebase + fj[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int col = colb + j;
+    const bool valid = rvalid && col >= cmin && col < cmax;
+    const double x = valid ? xs[j] : 0.0;
+    double* cp = g.C + cbase + (int64_t)(col + coff) * ldcv;
+    if constexpr (!CPLX) {
+      if (valid) {
+        double v = x;
+        if (!alpha_one) v = g.sc.alpha_re * x;
+        if (!first_pass) v += cv[j];
+        else if (!g.sc.beta_zero) v = fma(g.sc.beta_re, cv[j], v);
+        *cp = v;
+      }
+    } else {
+      const double xp = __shfl_xor_sync(0xFFFFFFFFu, x, 1);
+      const double cpn = __shfl_xor_sync(0xFFFFFFFFu, cv[j], 1);
+      if (valid) {
+        const double sgn = (rr & 1) ? 1.0 : -1.0;  // im row: +, re row: -
+        double v = fma(g.sc.alpha_re, x, sgn * g.sc.alpha_im * xp);
+        if (!first_pass) v += cv[j];
+        else if (!g.sc.beta_zero) v = fma(g.sc.beta_re, cv[j], fma(sgn * g.sc.beta_im, cpn, v));
+        *cp = v;
+      }
+    }
+  }
+}
+
 // SF > 0: the slice count is the compile-time constant SF (the MMA issue loop
 // unrolls completely); SF == 0: any slice count g.s with this tile width.
 // CPLX: complex instances (compile-time, so that each version carries only
 // its own epilogue).
-template <int BN, int SF, bool CPLX>
+// DB: two TMEM copies of the level accumulators (2 s BN <= 512), the
+// epilogue takes a finished tile whole while the MMAs fill the other copy.
+template <int BN, int SF, bool CPLX, bool DB>
 __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmArgs g) {
   constexpr int COLS = BN / 2;  // output columns per epilogue thread
+  // The 6-slice tile (40 accumulators per thread) is register-bound: it keeps
+  // the compact conversion and drains one level at a time.
+  constexpr bool kFastConv = SF != 6;
+  constexpr bool kMayPair = SF != 6;
   constexpr int BTILE = BN * kLineBytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -37,6 +104,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
       mbar_init(&S.a_empty[i], 1);
     }
     for (int i = 0; i < s; ++i) mbar_init(&S.lvl_full[i], 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&S.acc_full[i], 1);
+      mbar_init(&S.acc_empty[i], kEpiWarps);
+    }
     mbar_init(&S.tmem_free, kEpiWarps);
     mbar_init(&S.mma_done, 1);
     S.abort_flag = 0;
@@ -118,7 +189,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
         if (!unit_tiles(g, U, &at_, &bt_, &ablk_)) continue;
         const int npass = unit_passes(g, U);
         for (int c = 0; c < npass && ok; ++c, ++passc) {
-          if (passc > 0 && !mbar_wait(&S.tmem_free, (passc - 1) & 1, abort_flag)) {
+          // accumulator copy of this pass (always 0 without double buffering)
+          const uint32_t buf_off = DB ? (passc & 1) * (uint32_t)(s * BN) : 0u;
+          bool free_ok = true;
+          if constexpr (DB) {
+            if (passc >= 2)
+              free_ok = mbar_wait(&S.acc_empty[passc & 1], ((passc >> 1) - 1) & 1, abort_flag);
+          } else {
+            if (passc > 0) free_ok = mbar_wait(&S.tmem_free, (passc - 1) & 1, abort_flag);
+          }
+          if (!free_ok) {
             record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_ACC_EMPTY, (int)u);
             *abort_flag = 1;
             ok = false;
@@ -154,7 +234,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
               const int n1 = ncat > 256 ? ncat - 256 : 0;
               const uint32_t id0 = make_idesc(BM, ncat > 256 ? 256 : ncat);
               const uint32_t id1 = make_idesc(BM, n1 > 0 ? n1 : 16);
-              const uint32_t d0 = tmem_base + p * BN;
+              const uint32_t d0 = tmem_base + buf_off + p * BN;
               constexpr uint64_t kB256 = (256 * kLineBytes) >> 4;
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk) {
@@ -166,7 +246,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
               }
               acc0 = 1u;
               umma_commit(&S.a_empty[slot]);
-              if (last_kb) umma_commit(&S.lvl_full[p]);  // level p+2 is complete
+              if (!DB && last_kb) umma_commit(&S.lvl_full[p]);  // level p+2 is complete
               if (++slot == NA) {
                 slot = 0;
                 aphase ^= 1;
@@ -174,6 +254,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
             }
             if (!ok) break;
             umma_commit(&S.b_empty[buf]);
+            if (DB && last_kb) umma_commit(&S.acc_full[passc & 1]);  // the whole tile is done
           }
         }
       }
@@ -203,7 +284,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
       const int32_t* ma = g.metaA + (int64_t)ablk * kMetaStride;
       const int32_t* mb = g.metaB + (int64_t)U.b_blk * kMetaStride;
       const int e_i = ma[row];
-      const int F = ma[128 + row] + mb[256] + 1;
+      // frame: the row's norm exponent plus the largest one of the B block
+      int rbmax = -126;
+      for (int c = lane; c < BN; c += 32) rbmax = max(rbmax, mb[128 + c]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rbmax = max(rbmax, __shfl_xor_sync(0xFFFFFFFFu, rbmax, o));
+      const int F = ma[128 + row] + rbmax + 1;
       // output rows/columns of this thread
       int rr, inst_pos, cmin, cmax, coff;
       bool rvalid;
@@ -231,15 +317,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
       const int64_t ldcv = CPLX ? 2 * in.ldc : in.ldc;
       const int Ebase = F - 62 + e_i - 2 * g.beta;
       const int npass = unit_passes(g, U);
-      for (int c = 0; c < max(npass, 1) && ok; ++c) {
-        long long acc[COLS];
-#pragma unroll
-        for (int j = 0; j < COLS; ++j) acc[j] = 0;
-        if (npass > 0) {
-#pragma unroll 1
-          for (int lv = 0; lv < s; ++lv) {
+      if constexpr (DB) {
+        // ---- double-buffered TMEM: take the finished tile whole, 8 columns at a time
+        for (int c = 0; c < max(npass, 1) && ok; ++c) {
+          const uint32_t b = passc & 1;
+          if (npass > 0) {
             bool got = true;
-            if (lane == 0) got = mbar_wait(&S.lvl_full[lv], passc & 1, abort_flag);
+            if (lane == 0) got = mbar_wait(&S.acc_full[b], (passc >> 1) & 1, abort_flag);
             got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
             if (!got) {
               if (lane == 0) {
@@ -250,29 +334,100 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
               break;
             }
             tc_fence_after();
-            int sh = 62 - F - g.beta * lv;
+          }
+          const uint32_t tb = tq + b * (uint32_t)(s * BN);
+#pragma unroll 1
+          for (int j0 = 0; j0 < COLS; j0 += 8) {
+            long long acc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] = 0;
+            if (npass > 0) {
+              // all levels of the 8 columns in flight at once (compile-time slice
+              // counts), then the exact fixed-point sum
+              constexpr int NV = SF > 0 ? SF : 1;
+              uint32_t v[NV][8];
+              if constexpr (SF > 0) {
+#pragma unroll
+                for (int lv = 0; lv < SF; ++lv) tmem_ld8(tb + lv * BN + j0, v[lv]);
+                tmem_ld_wait();
+              }
+#pragma unroll
+              for (int lv = 0; lv < (SF > 0 ? SF : kMaxSlices); ++lv) {
+                if (SF == 0 && lv >= s) break;
+                uint32_t(&vl)[8] = v[SF > 0 ? lv : 0];
+                if constexpr (SF == 0) {
+                  tmem_ld8(tb + lv * BN + j0, vl);
+                  tmem_ld_wait();
+                }
+                int sh = 62 - F - g.beta * lv;
+                sh = max(-63, min(62, sh));
+                const int lsh = sh > 0 ? sh : 0, rsh = sh < 0 ? -sh : 0;
+                const long long rnd = rsh > 0 ? (1ll << (rsh - 1)) : 0ll;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  const long long L = (long long)__float2int_rn(__uint_as_float(vl[j]));
+                  acc[j] += ((L << lsh) + rnd) >> rsh;
+                }
+              }
+            }
+            epi_store8<CPLX, kFastConv>(g, acc, mb, col0 + j0, rvalid, cmin, cmax, coff, cbase, ldcv, Ebase,
+                             c == 0, alpha_one, rr);
+          }
+          if (npass > 0) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.acc_empty[b]);
+            ++passc;
+          }
+        }
+        continue;
+      }
+      for (int c = 0; c < max(npass, 1) && ok; ++c) {
+        long long acc[COLS];
+#pragma unroll
+        for (int j = 0; j < COLS; ++j) acc[j] = 0;
+        if (npass > 0) {
+          // Levels are drained as they complete. With beta <= 6 two adjacent
+          // levels first combine exactly in 32 bits (|L_t 2^beta + L_t+1| <
+          // 2^30 + 2^24), which halves the 64-bit shifts and adds.
+          const bool pairs = kMayPair && g.beta <= 6;
+#pragma unroll 1
+          for (int lv = 0; lv < s;) {
+            const int nlv = (pairs && lv + 1 < s) ? 2 : 1;
+            bool got = true;
+            if (lane == 0) {
+              got = mbar_wait(&S.lvl_full[lv], passc & 1, abort_flag);
+              if (got && nlv == 2) got = mbar_wait(&S.lvl_full[lv + 1], passc & 1, abort_flag);
+            }
+            got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
+            if (!got) {
+              if (lane == 0) {
+                record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_ACC_FULL, (int)u);
+                *abort_flag = 1;
+              }
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const int lvl = lv + nlv - 1;  // the combined value sits at this level's weight
+            int sh = 62 - F - g.beta * lvl;
             sh = max(-63, min(62, sh));
             const int lsh = sh > 0 ? sh : 0, rsh = sh < 0 ? -sh : 0;
             const long long rnd = rsh > 0 ? (1ll << (rsh - 1)) : 0ll;
 #pragma unroll
-            for (int j0 = 0; j0 < COLS; j0 += 16) {
+            for (int j0 = 0; j0 < COLS; j0 += 8) {
               uint32_t v0[8], v1[8];
               tmem_ld8(tq + lv * BN + j0, v0);
-              if (j0 + 8 < COLS) tmem_ld8(tq + lv * BN + j0 + 8, v1);
+              if (nlv == 2) tmem_ld8(tq + (lv + 1) * BN + j0, v1);
               tmem_ld_wait();
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
-                const long long L = (long long)__float2int_rn(__uint_as_float(v0[j]));
-                acc[j0 + j] += ((L << lsh) + rnd) >> rsh;
-              }
-              if (j0 + 8 < COLS) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                  const long long L = (long long)__float2int_rn(__uint_as_float(v1[j]));
-                  acc[j0 + 8 + j] += ((L << lsh) + rnd) >> rsh;
-                }
+                int L = __float2int_rn(__uint_as_float(v0[j]));
+                if (nlv == 2) L = (L << g.beta) + __float2int_rn(__uint_as_float(v1[j]));
+                acc[j0 + j] += (((long long)L << lsh) + rnd) >> rsh;
               }
             }
+            lv += nlv;
           }
           if (!ok) break;
           tc_fence_before();
@@ -281,48 +436,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
           ++passc;
         }
         // ---- exact conversion, alpha/beta, store (TMEM already free: overlaps the next MMAs).
-        // Each group of 8 columns first loads its 8 old C values and 8 column
-        // exponents, then converts and stores: all loads are in flight together
-        // instead of each one waiting behind the previous column's store.
-        const bool first_pass = c == 0;
-        const bool need_c = !first_pass || !g.sc.beta_zero;
         for (int j0 = 0; j0 < COLS; j0 += 8) {
-          double cv[8];
-          int fj[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int col = col0 + j0 + j;
-            const bool valid = rvalid && col >= cmin && col < cmax;
-            fj[j] = __ldg(mb + col);
-            cv[j] = (valid && need_c) ? g.C[cbase + (int64_t)(col + coff) * ldcv] : 0.0;
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int col = col0 + j0 + j;
-            const bool valid = rvalid && col >= cmin && col < cmax;
-            const double x = valid ? fixed_to_double(acc[j], Ebase + fj[j]) : 0.0;
-            double* cp = g.C + cbase + (int64_t)(col + coff) * ldcv;
-            if constexpr (!CPLX) {
-              if (valid) {
-                double v = x;
-                if (!alpha_one) v = g.sc.alpha_re * x;
-                if (!first_pass) v += cv[j];
-                else if (!g.sc.beta_zero) v = fma(g.sc.beta_re, cv[j], v);
-                *cp = v;
-              }
-            } else {
-              const double xp = __shfl_xor_sync(0xFFFFFFFFu, x, 1);
-              const double cpn = __shfl_xor_sync(0xFFFFFFFFu, cv[j], 1);
-              if (valid) {
-                const double sgn = (rr & 1) ? 1.0 : -1.0;  // im row: +, re row: -
-                double v = fma(g.sc.alpha_re, x, sgn * g.sc.alpha_im * xp);
-                if (!first_pass) v += cv[j];
-                else if (!g.sc.beta_zero)
-                  v = fma(g.sc.beta_re, cv[j], fma(sgn * g.sc.beta_im, cpn, v));
-                *cp = v;
-              }
-            }
-          }
+          epi_store8<CPLX, kFastConv>(g, *reinterpret_cast<const long long(*)[8]>(acc), mb, col0 + j0,
+                           rvalid, cmin, cmax, coff, cbase, ldcv, Ebase, c == 0, alpha_one, rr);
           // rotate the next 8 accumulators into place (keeps the loop body small)
 #pragma unroll
           for (int j = 0; j + 8 < COLS; ++j) acc[j] = acc[j + 8];
@@ -343,23 +459,24 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
 
 // Same for the GEMM kernel template arguments: the tile width BN (from s)
 // and the compile-time slice count (3, 6 and 9 have unrolled versions).
-#define BG_DISPATCH_GEMM(s, ...)                                           \
-  switch (s) {                                                             \
-    case 3: { constexpr int BNV = 128, SFV = 3; __VA_ARGS__; }             \
-    case 6: { constexpr int BNV = 80, SFV = 6; __VA_ARGS__; }              \
-    case 9: { constexpr int BNV = 48, SFV = 9; __VA_ARGS__; }              \
-    case 1: case 2: case 4: { constexpr int BNV = 128, SFV = 0; __VA_ARGS__; } \
-    case 5: { constexpr int BNV = 96, SFV = 0; __VA_ARGS__; }              \
-    case 7: case 8: { constexpr int BNV = 64, SFV = 0; __VA_ARGS__; }      \
-    case 10: { constexpr int BNV = 48, SFV = 0; __VA_ARGS__; }             \
-    case 11: case 12: { constexpr int BNV = 32, SFV = 0; __VA_ARGS__; }    \
-    default: return cudaErrorInvalidValue;                                 \
+#define BG_DISPATCH_GEMM(s, ...)                                                    \
+  switch (s) {                                                                      \
+    case 3: { constexpr int BNV = bn_for(3), SFV = 3; constexpr bool DBV = true; __VA_ARGS__; } \
+    case 6: { constexpr int BNV = bn_for(6), SFV = 6; constexpr bool DBV = false; __VA_ARGS__; } \
+    case 9: { constexpr int BNV = bn_for(9), SFV = 9; constexpr bool DBV = false; __VA_ARGS__; } \
+    case 1: case 2: { constexpr int BNV = 128, SFV = 0; constexpr bool DBV = true; __VA_ARGS__; } \
+    case 4: { constexpr int BNV = 64, SFV = 0; constexpr bool DBV = true; __VA_ARGS__; }   \
+    case 5: { constexpr int BNV = 48, SFV = 0; constexpr bool DBV = true; __VA_ARGS__; }   \
+    case 7: case 8: { constexpr int BNV = 64, SFV = 0; constexpr bool DBV = false; __VA_ARGS__; } \
+    case 10: { constexpr int BNV = 48, SFV = 0; constexpr bool DBV = false; __VA_ARGS__; } \
+    case 11: case 12: { constexpr int BNV = 32, SFV = 0; constexpr bool DBV = false; __VA_ARGS__; } \
+    default: return cudaErrorInvalidValue;                                          \
   }
 
 template <bool CPLX>
 cudaError_t launch_gemm_t(int s, int grid, size_t smem, cudaStream_t st, const GemmArgs& g) {
   BG_DISPATCH_GEMM(s, {
-    split_gemm_kernel<BNV, SFV, CPLX><<<grid, kGemmThreads, smem, st>>>(g);
+    split_gemm_kernel<BNV, SFV, CPLX, DBV><<<grid, kGemmThreads, smem, st>>>(g);
     return cudaGetLastError();
   });
 }
@@ -367,7 +484,7 @@ cudaError_t launch_gemm_t(int s, int grid, size_t smem, cudaStream_t st, const G
 template <bool CPLX>
 cudaError_t set_attr_t(int s) {
   BG_DISPATCH_GEMM(s, {
-    return cudaFuncSetAttribute(split_gemm_kernel<BNV, SFV, CPLX>,
+    return cudaFuncSetAttribute(split_gemm_kernel<BNV, SFV, CPLX, DBV>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
   });
 }

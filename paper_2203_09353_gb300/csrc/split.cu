@@ -150,6 +150,10 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
         in = isA ? a.instA[a.orderA[J.pos + li]] : a.instB[a.orderB[J.pos + li]];
         valid = isA ? line < (a.cplx ? 2 * in.m : in.m) : line < in.n;
       }
+      // rows of A / columns of B beyond the instance only meet discarded
+      // outputs: an item of 4 such lines is skipped (its tile rows keep
+      // whatever finite digits they hold; the planner zeroes them once)
+      if (!__any_sync(0xFFFFFFFFu, valid)) continue;
       double x[8];
       load8(a, isA, in, valid, line, kb * BK + 8 * cc, kv, x);
       unsigned long long mx = 0;
@@ -179,6 +183,7 @@ __global__ void __launch_bounds__(kSliceThreads) split_slice_kernel(const SliceA
         in = isA ? a.instA[a.orderA[J.pos + li]] : a.instB[a.orderB[J.pos + li]];
         valid = isA ? line < (a.cplx ? 2 * in.m : in.m) : line < in.n;
       }
+      if (!__any_sync(0xFFFFFFFFu, valid)) continue;
       const int e = s_e[l];
       double x[8];
       load8(a, isA, in, valid, line, kb * BK + 8 * cc, kv, x);
@@ -615,10 +620,14 @@ static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& t
       (e = dalloc(reinterpret_cast<void**>(&p->metaB), (size_t)std::max(blkB, 1) * kMetaStride * 4,
                   &p->bytes)) != cudaSuccess)
     return cuda_err(err, e, "split plan allocation");
-  // meta of blocks without slice jobs (k == 0) must read as zero lines
+  // meta of blocks without slice jobs (k == 0) must read as zero lines; tile
+  // rows of lines beyond an instance are never written by the slicer and
+  // start out as zero digits
   if ((e = cudaMemset(p->metaA, 0, (size_t)std::max(blkA, 1) * kMetaStride * 4)) != cudaSuccess ||
-      (e = cudaMemset(p->metaB, 0, (size_t)std::max(blkB, 1) * kMetaStride * 4)) != cudaSuccess)
-    return cuda_err(err, e, "split plan meta clear");
+      (e = cudaMemset(p->metaB, 0, (size_t)std::max(blkB, 1) * kMetaStride * 4)) != cudaSuccess ||
+      (e = cudaMemset(p->tilesA, 0, (size_t)tileA * kATileBytes)) != cudaSuccess ||
+      (e = cudaMemset(p->tilesB, 0, (size_t)tileB * btile)) != cudaSuccess)
+    return cuda_err(err, e, "split plan workspace clear");
   return BG_OK;
 }
 
@@ -854,8 +863,10 @@ bg_status split_fixed_in_scratch(bg_dtype dt, const bg_precision& pr, int64_t m,
   p.n_units = (int64_t)t.units.size();
   p.count = batch;
   cudaError_t e;
-  // the scratch keeps the previous call's contents: clear the error word and the meta stores
-  if ((e = cudaMemsetAsync(base, 0, o_jobs, st)) != cudaSuccess)
+  // the scratch keeps the previous call's contents: clear the error word, the
+  // meta stores and the digit tiles (rows beyond an instance are not written)
+  if ((e = cudaMemsetAsync(base, 0, o_jobs, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(base + o_ta, 0, off - o_ta, st)) != cudaSuccess)
     return cuda_err(err, e, "static scratch clear");
   struct Piece { size_t off; const void* src; size_t bytes; };
   const Piece pieces[] = {{o_jobs, t.jobs.data(), t.jobs.size() * sizeof(SliceJob)},
@@ -989,6 +1000,8 @@ bg_status split_chain_create(SplitPlan** out, bg_dtype dt, const bg_precision& p
   }
   cudaMemset(p->metaA, 0, (size_t)std::max(blkA, 1) * kMetaStride * 4);
   cudaMemset(p->metaB, 0, (size_t)std::max(blkB, 1) * kMetaStride * 4);
+  cudaMemset(p->tilesA, 0, (size_t)tileA * kATileBytes);
+  cudaMemset(p->tilesB, 0, (size_t)tileB * btile);
   grids(p);
   finish_desc(p);
   *out = p;

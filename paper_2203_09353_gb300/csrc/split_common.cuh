@@ -16,8 +16,8 @@ constexpr int BM = 128, BK = 64;
 constexpr int kATileBytes = BM * BK * 2;  // 16 KiB: one A plane of one k-block
 constexpr int kLineBytes = BK * 2;        // 128 bytes: one row of a tile
 constexpr int kMaxAStages = 8;
-constexpr int kGemmThreads = 320;
-constexpr int kEpiWarps = 8;
+// Split GEMM CTA: producer warp, MMA warp, then 4 H epilogue warps.
+__host__ __device__ constexpr int gemm_threads(int h) { return 64 + 128 * h; }
 constexpr int kMetaStride = 264;  // int32 per block: e[128], R[128] (then padding)
 constexpr int kTmemCols = 512;
 constexpr int kSliceThreads = 256;

@@ -74,9 +74,14 @@ __device__ __forceinline__ void epi_store8(const GemmArgs& g, const long long (&
 // its own epilogue).
 // DB: two TMEM copies of the level accumulators (2 s BN <= 512), the
 // epilogue takes a finished tile whole while the MMAs fill the other copy.
-template <int BN, int SF, bool CPLX, bool DB>
-__global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmArgs g) {
-  constexpr int COLS = BN / 2;  // output columns per epilogue thread
+// H: epilogue warps per TMEM lane quadrant; each owns BN / H of the tile's
+// columns (more warps hide more of the epilogue's latency, fewer registers
+// per thread).
+template <int BN, int SF, bool CPLX, bool DB, int H>
+__global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const GemmArgs g) {
+  static_assert(BN % (8 * H) == 0, "epilogue column groups of 8");
+  constexpr int COLS = BN / H;  // output columns per epilogue thread
+  constexpr int kEpi = 4 * H;   // epilogue warps
   // The 6-slice tile (40 accumulators per thread) is register-bound: it keeps
   // the compact conversion and drains one level at a time.
   constexpr bool kFastConv = SF != 6;
@@ -106,9 +111,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
     for (int i = 0; i < s; ++i) mbar_init(&S.lvl_full[i], 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(&S.acc_full[i], 1);
-      mbar_init(&S.acc_empty[i], kEpiWarps);
+      mbar_init(&S.acc_empty[i], kEpi);
     }
-    mbar_init(&S.tmem_free, kEpiWarps);
+    mbar_init(&S.tmem_free, kEpi);
     mbar_init(&S.mma_done, 1);
     S.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -265,7 +270,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
   } else {
     // ---------------- epilogue: drain levels, recombine, free TMEM, store
     const int quad = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int half = (warp - 2) >> 2;  // column group of this warp within its quadrant
     const int row = quad * 32 + lane;
     const int col0 = half * COLS;
     const uint32_t tq = tmem_base + ((uint32_t)(quad * 32) << 16) + col0;
@@ -461,22 +466,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const GemmA
 // and the compile-time slice count (3, 6 and 9 have unrolled versions).
 #define BG_DISPATCH_GEMM(s, ...)                                                    \
   switch (s) {                                                                      \
-    case 3: { constexpr int BNV = bn_for(3), SFV = 3; constexpr bool DBV = true; __VA_ARGS__; } \
-    case 6: { constexpr int BNV = bn_for(6), SFV = 6; constexpr bool DBV = false; __VA_ARGS__; } \
-    case 9: { constexpr int BNV = bn_for(9), SFV = 9; constexpr bool DBV = false; __VA_ARGS__; } \
-    case 1: case 2: { constexpr int BNV = 128, SFV = 0; constexpr bool DBV = true; __VA_ARGS__; } \
-    case 4: { constexpr int BNV = 64, SFV = 0; constexpr bool DBV = true; __VA_ARGS__; }   \
-    case 5: { constexpr int BNV = 48, SFV = 0; constexpr bool DBV = true; __VA_ARGS__; }   \
-    case 7: case 8: { constexpr int BNV = 64, SFV = 0; constexpr bool DBV = false; __VA_ARGS__; } \
-    case 10: { constexpr int BNV = 48, SFV = 0; constexpr bool DBV = false; __VA_ARGS__; } \
-    case 11: case 12: { constexpr int BNV = 32, SFV = 0; constexpr bool DBV = false; __VA_ARGS__; } \
+    case 3: { constexpr int BNV = bn_for(3), SFV = 3, HV = 4; constexpr bool DBV = true; __VA_ARGS__; } \
+    case 6: { constexpr int BNV = bn_for(6), SFV = 6, HV = 2; constexpr bool DBV = false; __VA_ARGS__; } \
+    case 9: { constexpr int BNV = bn_for(9), SFV = 9, HV = 3; constexpr bool DBV = false; __VA_ARGS__; } \
+    case 1: case 2: { constexpr int BNV = 128, SFV = 0, HV = 2; constexpr bool DBV = true; __VA_ARGS__; } \
+    case 4: { constexpr int BNV = 64, SFV = 0, HV = 2; constexpr bool DBV = true; __VA_ARGS__; }   \
+    case 5: { constexpr int BNV = 48, SFV = 0, HV = 2; constexpr bool DBV = true; __VA_ARGS__; }   \
+    case 7: case 8: { constexpr int BNV = 64, SFV = 0, HV = 2; constexpr bool DBV = false; __VA_ARGS__; } \
+    case 10: { constexpr int BNV = 48, SFV = 0, HV = 2; constexpr bool DBV = false; __VA_ARGS__; } \
+    case 11: case 12: { constexpr int BNV = 32, SFV = 0, HV = 2; constexpr bool DBV = false; __VA_ARGS__; } \
     default: return cudaErrorInvalidValue;                                          \
   }
 
 template <bool CPLX>
 cudaError_t launch_gemm_t(int s, int grid, size_t smem, cudaStream_t st, const GemmArgs& g) {
   BG_DISPATCH_GEMM(s, {
-    split_gemm_kernel<BNV, SFV, CPLX, DBV><<<grid, kGemmThreads, smem, st>>>(g);
+    split_gemm_kernel<BNV, SFV, CPLX, DBV, HV><<<grid, gemm_threads(HV), smem, st>>>(g);
     return cudaGetLastError();
   });
 }
@@ -484,7 +489,7 @@ cudaError_t launch_gemm_t(int s, int grid, size_t smem, cudaStream_t st, const G
 template <bool CPLX>
 cudaError_t set_attr_t(int s) {
   BG_DISPATCH_GEMM(s, {
-    return cudaFuncSetAttribute(split_gemm_kernel<BNV, SFV, CPLX, DBV>,
+    return cudaFuncSetAttribute(split_gemm_kernel<BNV, SFV, CPLX, DBV, HV>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
   });
 }

@@ -385,68 +385,68 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
             ++passc;
           }
         }
-        continue;
-      }
-      for (int c = 0; c < max(npass, 1) && ok; ++c) {
-        long long acc[COLS];
+      } else {
+        for (int c = 0; c < max(npass, 1) && ok; ++c) {
+          long long acc[COLS];
 #pragma unroll
-        for (int j = 0; j < COLS; ++j) acc[j] = 0;
-        if (npass > 0) {
-          // Levels are drained as they complete. With beta <= 6 two adjacent
-          // levels first combine exactly in 32 bits (|L_t 2^beta + L_t+1| <
-          // 2^30 + 2^24), which halves the 64-bit shifts and adds.
-          const bool pairs = kMayPair && g.beta <= 6;
+          for (int j = 0; j < COLS; ++j) acc[j] = 0;
+          if (npass > 0) {
+            // Levels are drained as they complete. With beta <= 6 two adjacent
+            // levels first combine exactly in 32 bits (|L_t 2^beta + L_t+1| <
+            // 2^30 + 2^24), which halves the 64-bit shifts and adds.
+            const bool pairs = kMayPair && g.beta <= 6;
 #pragma unroll 1
-          for (int lv = 0; lv < s;) {
-            const int nlv = (pairs && lv + 1 < s) ? 2 : 1;
-            bool got = true;
-            if (lane == 0) {
-              got = mbar_wait(&S.lvl_full[lv], passc & 1, abort_flag);
-              if (got && nlv == 2) got = mbar_wait(&S.lvl_full[lv + 1], passc & 1, abort_flag);
-            }
-            got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
-            if (!got) {
+            for (int lv = 0; lv < s;) {
+              const int nlv = (pairs && lv + 1 < s) ? 2 : 1;
+              bool got = true;
               if (lane == 0) {
-                record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_ACC_FULL, (int)u);
-                *abort_flag = 1;
+                got = mbar_wait(&S.lvl_full[lv], passc & 1, abort_flag);
+                if (got && nlv == 2) got = mbar_wait(&S.lvl_full[lv + 1], passc & 1, abort_flag);
               }
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const int lvl = lv + nlv - 1;  // the combined value sits at this level's weight
-            int sh = 62 - F - g.beta * lvl;
-            sh = max(-63, min(62, sh));
-            const int lsh = sh > 0 ? sh : 0, rsh = sh < 0 ? -sh : 0;
-            const long long rnd = rsh > 0 ? (1ll << (rsh - 1)) : 0ll;
-#pragma unroll
-            for (int j0 = 0; j0 < COLS; j0 += 8) {
-              uint32_t v0[8], v1[8];
-              tmem_ld8(tq + lv * BN + j0, v0);
-              if (nlv == 2) tmem_ld8(tq + (lv + 1) * BN + j0, v1);
-              tmem_ld_wait();
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                int L = __float2int_rn(__uint_as_float(v0[j]));
-                if (nlv == 2) L = (L << g.beta) + __float2int_rn(__uint_as_float(v1[j]));
-                acc[j0 + j] += (((long long)L << lsh) + rnd) >> rsh;
+              got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
+              if (!got) {
+                if (lane == 0) {
+                  record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_ACC_FULL, (int)u);
+                  *abort_flag = 1;
+                }
+                ok = false;
+                break;
               }
+              tc_fence_after();
+              const int lvl = lv + nlv - 1;  // the combined value sits at this level's weight
+              int sh = 62 - F - g.beta * lvl;
+              sh = max(-63, min(62, sh));
+              const int lsh = sh > 0 ? sh : 0, rsh = sh < 0 ? -sh : 0;
+              const long long rnd = rsh > 0 ? (1ll << (rsh - 1)) : 0ll;
+#pragma unroll
+              for (int j0 = 0; j0 < COLS; j0 += 8) {
+                uint32_t v0[8], v1[8];
+                tmem_ld8(tq + lv * BN + j0, v0);
+                if (nlv == 2) tmem_ld8(tq + (lv + 1) * BN + j0, v1);
+                tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  int L = __float2int_rn(__uint_as_float(v0[j]));
+                  if (nlv == 2) L = (L << g.beta) + __float2int_rn(__uint_as_float(v1[j]));
+                  acc[j0 + j] += (((long long)L << lsh) + rnd) >> rsh;
+                }
+              }
+              lv += nlv;
             }
-            lv += nlv;
+            if (!ok) break;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.tmem_free);
+            ++passc;
           }
-          if (!ok) break;
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&S.tmem_free);
-          ++passc;
-        }
-        // ---- exact conversion, alpha/beta, store (TMEM already free: overlaps the next MMAs).
-        for (int j0 = 0; j0 < COLS; j0 += 8) {
-          epi_store8<CPLX, kFastConv>(g, *reinterpret_cast<const long long(*)[8]>(acc), mb, col0 + j0,
-                           rvalid, cmin, cmax, coff, cbase, ldcv, Ebase, c == 0, alpha_one, rr);
-          // rotate the next 8 accumulators into place (keeps the loop body small)
+          // ---- exact conversion, alpha/beta, store (TMEM already free: overlaps the next MMAs).
+          for (int j0 = 0; j0 < COLS; j0 += 8) {
+            epi_store8<CPLX, kFastConv>(g, *reinterpret_cast<const long long(*)[8]>(acc), mb, col0 + j0,
+                             rvalid, cmin, cmax, coff, cbase, ldcv, Ebase, c == 0, alpha_one, rr);
+            // rotate the next 8 accumulators into place (keeps the loop body small)
 #pragma unroll
-          for (int j = 0; j + 8 < COLS; ++j) acc[j] = acc[j + 8];
+            for (int j = 0; j + 8 < COLS; ++j) acc[j] = acc[j + 8];
+          }
         }
       }
     }

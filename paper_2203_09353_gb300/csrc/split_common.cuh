@@ -22,7 +22,7 @@ constexpr int kMetaStride = 264;  // int32 per block: e[128], R[128] (then paddi
 constexpr int kTmemCols = 512;
 constexpr int kSliceThreads = 256;
 // Largest FP64 footprint of one slicer job (see split_jobs).
-constexpr int64_t kSliceJobBytes = 131072;
+constexpr int64_t kSliceJobBytes = 65536;
 constexpr int kMaxDynSmem = 232448;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any single wait
 

@@ -10,6 +10,7 @@
 * 960 + 64 complex walkers (n = 256 and 1024) with their Haar pools: two
   chained steps, sampled walkers step-locally against the oracle, and the
   unitarity drift of every walker.
+* the rectangular operator shapes of Sec. 3 (S = 13, 15, 17 spins).
 """
 import numpy as np
 import pytest
@@ -89,6 +90,31 @@ def test_loguniform_size_mix_20000_all_modes(gpu, loguniform_20000):
     for s in (3, 6, 9):
         bg.rel_err("r64", dtab, A, B, out[f"split{s}"], out["fp64"], err, b.count)
         assert float(err.max()) <= TOL_SPLIT[s] + TOL_FP64, (s, float(err.max()))
+
+
+@pytest.mark.parametrize("S", [13, 15, 17])
+def test_sec3_rectangular_shapes(gpu, S):
+    """The operator shapes of Sec. 3 for S spins: M = N = 2^(S - floor(S/2)),
+    K = 2^floor(S/2), complex, in one grouped call per mode."""
+    rng = np.random.default_rng(S)
+    M = N = 2 ** (S - S // 2)
+    K = 2 ** (S // 2)
+    shapes = [(M, N, K)] * 3
+    table, la, lb, lc = synth.pack_table(shapes)
+    A = synth.complex_gaussian(rng, la)
+    B = synth.complex_gaussian(rng, lb)
+    C = synth.complex_gaussian(rng, lc)
+    b = synth.Batch(f"sec3_S{S}", "c128", table, A, B, C, 1.0 + 0.5j, 0.5)
+    ref = oracle_batch(b)
+    for prec, tol in ((None, TOL_FP64), (bg.precision("split", 3), TOL_SPLIT[3]),
+                      (bg.precision("split", 6), TOL_SPLIT[6]),
+                      (bg.precision("split", 9), TOL_SPLIT[9])):
+        plan = bg.batched_gemm_plan("c128", table, prec)
+        Cd = dev(C)
+        bg.batched_gemm_grouped(plan, dev(A), dev(B), Cd, b.alpha, b.beta)
+        e = errors(b, host(Cd), ref)
+        assert e.max() <= tol, (S, prec and prec.slices, e.max())
+        plan.close()
 
 
 def test_chain_1024_walkers_two_steps(gpu):

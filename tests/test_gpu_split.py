@@ -216,3 +216,32 @@ def test_split_runs_leave_no_device_error(gpu):
 def test_fp64_peak_probe(gpu):
     t = bg.probe_fp64_peak()
     assert 0.1 < t < 100.0
+
+
+@pytest.mark.parametrize("s", [3, 4, 6, 9])
+def test_long_k_multipass_sampled_rows(gpu, s):
+    """Two 1024 x 768 instances with k = 2560: every mode then needs several
+    exact-sum passes over k (3 slices: 768 per pass, 6 slices: 512, 9 slices:
+    1472), each pass added into C. Sampled rows are checked against the oracle
+    computing just those rows (m = 1 sub-problems)."""
+    rng = np.random.default_rng(40 + s)
+    m, n, k = 1024, 768, 2560
+    count = 2
+    A = rng.uniform(-1, 1, m * k * count)
+    B = rng.uniform(-1, 1, k * n * count)
+    C = rng.uniform(-1, 1, m * n * count)
+    Cd = dev(C)
+    bg.batched_gemm_fixed("r64", m, n, k, 1.0, dev(A), m, m * k, dev(B), k, k * n, 0.5, Cd, m,
+                          m * n, count, split(s))
+    got = host(Cd)
+    for i in range(count):
+        a, b, c = A[i * m * k:], B[i * k * n:(i + 1) * k * n], C[i * m * n:]
+        for r in rng.choice(m, 6, replace=False):
+            ref = c[r:].copy()
+            oracle.gemm_fixed(1, n, k, 1.0, a[r:], m, 0, b, k, 0, 0.5, ref, m, 0, 1)
+            cols = np.arange(n) * m
+            row_ref = ref[cols]
+            row_got = got[i * m * n + r + cols]
+            # normwise for the row: ||c_r - ref_r|| / (||a_r|| ||B||)
+            den = np.linalg.norm(a[r::m][:k]) * np.linalg.norm(b)
+            assert np.linalg.norm(row_got - row_ref) / den <= TOL_SPLIT.get(s, 1e-6), (s, i, r)

@@ -3,7 +3,7 @@
 
 One step = one grouped call of the library on the whole synthetic batch (one
 persistent launch for FP64; slicer + tensor-core GEMM for split-BF16). The
-default workload is the precision configuration: 20000 square FP64 instances
+default workload is the log-uniform size mix: 20000 square FP64 instances
 with n drawn from {16, 32, 64, 128, 256, 512} (weights .3/.25/.2/.15/.07/.03),
 entries of magnitude 10^U(-4,4) with random signs, alpha = 1, beta = 0.5,
 seed 3. Every mode runs on the same batch: plain FP64 and split-BF16 with 3,
@@ -32,6 +32,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "batched GEMM TFLOP/s & roofline %: FP64 vs split-BF16 at same error"
+# the seeded synthetic workloads: a fixed n = 32 real batch, a complex n = 64
+# Hermitian x unitary batch, and the 20000-instance size mixes (U[-1,1] and
+# log-uniform magnitudes)
+WORKLOADS = ("fixed-n32", "complex-n64", "mix-uniform", "mix-loguniform")
 UNIT = "TFLOP/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
@@ -61,8 +65,8 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", type=int, choices=[1, 2, 3, 4], default=4)
-    p.add_argument("--count", type=int, default=20000, help="instances (configs 3/4)")
+    p.add_argument("--workload", choices=WORKLOADS, default="mix-loguniform")
+    p.add_argument("--count", type=int, default=20000, help="instances (the size mixes)")
     p.add_argument("--mode", default="split9", help="headline mode: fp64 or splitS")
     p.add_argument("--modes", default="fp64,split3,split6,split9")
     p.add_argument("--fp64-steps", type=int, default=3)
@@ -84,21 +88,21 @@ def peaks():
     return dict(FALLBACK_PEAKS), "fallback"
 
 
-def make_batch(config: int, count: int, rank: int):
+def make_batch(workload: str, count: int, rank: int):
     from paper_2203_09353_gb300 import synth
-    if config == 1:
-        return synth.config1(), "config1: 64 real FP64 instances n=32, U[-1,1], seed 0, C=AB"
-    if config == 2:
-        return synth.config2(), ("config2: 4096 complex128 instances n=64, A Hermitian, "
+    if workload == "fixed-n32":
+        return synth.fixed_real_n32(), "64 real FP64 instances n=32, U[-1,1], seed 0, C=AB"
+    if workload == "complex-n64":
+        return synth.hermitian_unitary_c128(), ("4096 complex128 instances n=64, A Hermitian, "
                                  "B Haar unitary, seed 1, C=AB")
-    if config == 3:
+    if workload == "mix-uniform":
         seed = 2 + 1000 * rank
-        b = synth.mixed_batch(seed, count, "uniform", 1.0, 0.5, name=f"config3_{count}")
-        return b, (f"config3: {count} real FP64 instances n in {{16..512}} "
+        b = synth.mixed_batch(seed, count, "uniform", 1.0, 0.5, name=f"size_mix_uniform_{count}")
+        return b, (f"{count} real FP64 instances n in {{16..512}} "
                    f"(w .3/.25/.2/.15/.07/.03), U[-1,1], alpha=1, beta=0.5, seed {seed}")
     seed = 3 + 1000 * rank
-    b = synth.mixed_batch(seed, count, "loguniform", 1.0, 0.5, name=f"config4_{count}")
-    return b, (f"config4: {count} real FP64 instances n in {{16..512}} "
+    b = synth.mixed_batch(seed, count, "loguniform", 1.0, 0.5, name=f"size_mix_loguniform_{count}")
+    return b, (f"{count} real FP64 instances n in {{16..512}} "
                f"(w .3/.25/.2/.15/.07/.03), |x| = 10^U(-4,4) random sign, alpha=1, beta=0.5, "
                f"seed {seed}")
 
@@ -334,7 +338,7 @@ def run_reference(args, world, rank, pg):
     """--impl reference: the CPU oracle, as it stands, on bounded samples of the workload."""
     if rank != 0:
         return
-    batch, desc = make_batch(args.config, args.count, 0)
+    batch, desc = make_batch(args.workload, args.count, 0)
     budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
     ids = calibrated_sample(batch, budget)
     times, flops, threads = [], 0.0, 1
@@ -378,7 +382,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     pk, pk_src = peaks()
-    batch, desc = make_batch(args.config, args.count, rank)
+    batch, desc = make_batch(args.workload, args.count, rank)
     log(f"generated {desc}")
     flops = batch.flops()
     job_flops = sum_over_ranks(pg, flops)  # every rank's shard counts toward the job
@@ -472,7 +476,7 @@ def main():
         del Cm
 
     # --- roofline of the dominant kernel of each mode
-    traffic_ok = args.config == 4 and split_sources_sha() == NCU_SOURCES_SHA
+    traffic_ok = args.workload == "mix-loguniform" and split_sources_sha() == NCU_SOURCES_SHA
     t = batch.table.astype(np.float64)
     esz = 16.0 if batch.dtype == "c128" else 8.0
     ab_elems = float(np.sum(t[:, 0] * t[:, 2] + t[:, 2] * t[:, 1]))

@@ -8,17 +8,17 @@ The paper runs no public dataset; its operands are the 2^S-sized complex
 operators of an S-spin transverse-field Ising chain (Sec. 3). These batches
 stand in for them with the same shapes (square powers of two) and the
 structure the workload has (Hermitian operators, unitary gates, a mix of
-sizes), one recipe per benchmark configuration:
+sizes), one recipe per workload:
 
-* ``config1``: 64 real instances, n = 32, entries U[-1, 1] (seed 0), alpha=1, beta=0.
-* ``config2``: 4096 complex instances, n = 64; A_i Hermitian, (G + G^H)/2 with
+* ``fixed_real_n32``: 64 real instances, n = 32, entries U[-1, 1] (seed 0), alpha=1, beta=0.
+* ``hermitian_unitary_c128``: 4096 complex instances, n = 64; A_i Hermitian, (G + G^H)/2 with
   G = X + iY, X, Y standard normal; B_i Haar unitary (QR of a complex Gaussian,
   columns multiplied by the phases of diag(R)); seed 1, alpha=1, beta=0.
-* ``config3``: 20000 real instances, n drawn from {16,...,512} with weights
+* ``size_mix_uniform``: 20000 real instances, n drawn from {16,...,512} with weights
   {.3,.25,.2,.15,.07,.03}, entries U[-1, 1], alpha=1, beta=0.5, seed 2.
-* ``config4``: the config-3 size mix drawn with seed 3, entries of magnitude
+* ``size_mix_loguniform``: the same size mix drawn with seed 3, entries of magnitude
   10^U(-4, 4) with a random sign (A, B and C), alpha=1, beta=0.5.
-* ``config5``: chained products C <- U_t C: a pool of Haar unitaries, a
+* ``annealing_chain``: chained products C <- U_t C: a pool of Haar unitaries, a
   [steps, walkers] pool-index table and a Haar-unitary start state per walker.
 
 Draw order (fixed so that every run sees the same numbers): sizes first
@@ -187,20 +187,20 @@ def fixed_uniform(batch: int, m: int, n: int, k: int, seed: int, dtype: str = "r
                  alpha, beta, meta={"fixed": (m, n, k, batch)})
 
 
-def config1() -> Batch:
+def fixed_real_n32() -> Batch:
     """64 real instances of n = 32, U[-1, 1] entries, seed 0, C = A B."""
     b = fixed_uniform(64, 32, 32, 32, seed=0, dtype="r64", alpha=1.0, beta=0.0,
-                      name="config1_r64_64x32")
+                      name="fixed_r64_64x32")
     return b
 
 
-def config2(batch: int = 4096, n: int = 64) -> Batch:
+def hermitian_unitary_c128(batch: int = 4096, n: int = 64) -> Batch:
     """Complex fixed batch: A_i Hermitian, B_i Haar unitary, seed 1, C = A B."""
     rng = np.random.default_rng(1)
     A = hermitian(rng, n, batch)
     B = haar_unitary(rng, n, batch)
     table, la, lb, lc = pack_table([(n, n, n)] * batch, align=1)
-    return Batch(f"config2_c128_{batch}x{n}", "c128", table, _col_major_flat(A),
+    return Batch(f"hermitian_unitary_c128_{batch}x{n}", "c128", table, _col_major_flat(A),
                  _col_major_flat(B), np.zeros(lc, dtype=np.complex128), 1.0, 0.0,
                  meta={"fixed": (n, n, n, batch)})
 
@@ -248,12 +248,12 @@ def mixed_batch(seed: int, count: int, values: str, alpha=1.0, beta=0.5, sizes=C
                  beta, meta={"sizes": ns})
 
 
-def config3(count: int = 20000) -> Batch:
-    return mixed_batch(2, count, "uniform", 1.0, 0.5, name=f"config3_grouped_{count}")
+def size_mix_uniform(count: int = 20000) -> Batch:
+    return mixed_batch(2, count, "uniform", 1.0, 0.5, name=f"size_mix_uniform_{count}")
 
 
-def config4(count: int = 20000) -> Batch:
-    return mixed_batch(3, count, "loguniform", 1.0, 0.5, name=f"config4_loguniform_{count}")
+def size_mix_loguniform(count: int = 20000) -> Batch:
+    return mixed_batch(3, count, "loguniform", 1.0, 0.5, name=f"size_mix_loguniform_{count}")
 
 
 @dataclass
@@ -274,7 +274,7 @@ class Chain:
         return int(self.idx.shape[1])
 
 
-def config5(walkers_small: int = 960, walkers_large: int = 64, n_small: int = 256,
+def annealing_chain(walkers_small: int = 960, walkers_large: int = 64, n_small: int = 256,
             n_large: int = 1024, steps: int = 200, pool_small: int = 64,
             pool_large: int = 16) -> Chain:
     """Seed-4 chain: Haar pools, a uniform pool-index table, Haar start states.

@@ -60,7 +60,7 @@ def test_chain_argument_checks(gpu):
 
 
 def test_fault_injection_env(gpu, monkeypatch):
-    b = synth.config1()
+    b = synth.fixed_real_n32()
     monkeypatch.setenv("BGEMM_FAULT", "launch")
     Cd = dev(b.C)
     m, n, k, cnt = b.fixed_shape()
@@ -76,7 +76,7 @@ def test_fault_injection_env(gpu, monkeypatch):
 def test_capture_rules(gpu):
     """Plans refuse to be built under capture; the FP64 fixed path can be captured and replayed."""
     import torch
-    b = synth.config1()
+    b = synth.fixed_real_n32()
     m, n, k, cnt = b.fixed_shape()
     A, B, C = dev(b.A), dev(b.B), dev(b.C)
     s = torch.cuda.Stream()
@@ -101,7 +101,7 @@ def test_capture_rules(gpu):
 
 
 def test_launch_counter(gpu):
-    b = synth.config3(count=50)
+    b = synth.size_mix_uniform(count=50)
     plan = bg.batched_gemm_plan("r64", b.table)
     A, B, C = dev(b.A), dev(b.B), dev(b.C)
     bg.launch_count(reset=True)

@@ -52,7 +52,7 @@ def oracle_chain(chain, steps):
 
 
 def small_chain():
-    return synth.config5(walkers_small=6, walkers_large=2, n_small=32, n_large=96, steps=5,
+    return synth.annealing_chain(walkers_small=6, walkers_large=2, n_small=32, n_large=96, steps=5,
                          pool_small=4, pool_large=3)
 
 

@@ -14,15 +14,15 @@ from gpu_util import TOL_FP64, dev, errors, host, oracle_batch, run_fixed, run_g
 pytestmark = pytest.mark.gpu
 
 
-def test_config1_fixed_r64(gpu):
-    b = synth.config1()
+def test_fixed_real_n32(gpu):
+    b = synth.fixed_real_n32()
     C = host(run_fixed(b))
     e = errors(b, C, oracle_batch(b))
     assert e.max() <= TOL_FP64, e.max()
 
 
-def test_config2_fixed_c128_reduced(gpu):
-    b = synth.config2(batch=96)
+def test_hermitian_unitary_c128_reduced(gpu):
+    b = synth.hermitian_unitary_c128(batch=96)
     C = host(run_fixed(b))
     e = errors(b, C, oracle_batch(b))
     assert e.max() <= TOL_FP64, e.max()
@@ -107,7 +107,7 @@ def test_empty_batch_is_noop(gpu):
 @pytest.mark.parametrize("config", [3, 4])
 def test_grouped_mixed_sizes_reduced(gpu, config):
     """Configs 3/4 size mix (all six classes present) at a reduced count, one persistent launch."""
-    b = synth.config3(count=160) if config == 3 else synth.config4(count=160)
+    b = synth.size_mix_uniform(count=160) if config == 3 else synth.size_mix_loguniform(count=160)
     assert set(np.unique(b.table[:, 0])) == set(synth.CONFIG3_SIZES)
     C, plan = run_grouped(b)
     assert plan.info()["launches_per_call"] == 1
@@ -144,7 +144,7 @@ def test_grouped_ragged_and_degenerate(gpu, dtype):
 
 
 def test_graph_replay_is_bitwise_deterministic(gpu):
-    b = synth.config3(count=80)
+    b = synth.size_mix_uniform(count=80)
     plan = bg.batched_gemm_plan("r64", b.table, None, bg.BG_PLAN_CAPTURE_GRAPH)
     A, B = dev(b.A), dev(b.B)
     outs = []
@@ -158,7 +158,7 @@ def test_graph_replay_is_bitwise_deterministic(gpu):
 
 
 def test_autotune_and_cache(gpu, tmp_path):
-    b = synth.config3(count=120)
+    b = synth.size_mix_uniform(count=120)
     cache = str(tmp_path / "tune.json")
     flags = bg.BG_PLAN_AUTOTUNE | bg.BG_PLAN_USE_CACHE
     plan = bg.batched_gemm_plan("r64", b.table, None, flags, cache)
@@ -179,7 +179,7 @@ def test_dmma_program_matches_oracle(gpu):
     import json
     import os
     import tempfile
-    b = synth.config3(count=60)
+    b = synth.size_mix_uniform(count=60)
     plan0 = bg.batched_gemm_plan("r64", b.table)
     keys = []
     for c in json.loads(plan0.describe())["classes"]:

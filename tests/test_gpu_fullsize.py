@@ -33,7 +33,7 @@ def _sample(count: int, every: int, seed: int) -> np.ndarray:
 
 
 def test_complex_hermitian_unitary_4096_all_instances(gpu):
-    b = synth.config2()
+    b = synth.hermitian_unitary_c128()
     assert b.count == 4096 and b.fixed_shape() == (64, 64, 64, 4096)
     ref = oracle_batch(b)
     A, B = dev(b.A), dev(b.B)
@@ -48,7 +48,7 @@ def test_complex_hermitian_unitary_4096_all_instances(gpu):
 
 
 def test_uniform_size_mix_20000_fp64_autotuned(gpu, tmp_path):
-    b = synth.config3()
+    b = synth.size_mix_uniform()
     assert b.count == 20000
     flags = bg.BG_PLAN_AUTOTUNE | bg.BG_PLAN_USE_CACHE
     plan = bg.batched_gemm_plan("r64", b.table, None, flags, str(tmp_path / "tune.json"))
@@ -62,7 +62,7 @@ def test_uniform_size_mix_20000_fp64_autotuned(gpu, tmp_path):
 
 @pytest.fixture(scope="module")
 def loguniform_20000():
-    return synth.config4()
+    return synth.size_mix_loguniform()
 
 
 def test_loguniform_size_mix_20000_all_modes(gpu, loguniform_20000):
@@ -120,7 +120,7 @@ def test_sec3_rectangular_shapes(gpu, S):
 def test_chain_1024_walkers_two_steps(gpu):
     import torch
     from test_gpu_chain import layout
-    ch = synth.config5()
+    ch = synth.annealing_chain()
     assert ch.walkers == 1024 and ch.steps == 200
     pool, pn, po, states, wo, gidx = layout(ch)
     dpool = dev(pool)

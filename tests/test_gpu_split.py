@@ -23,9 +23,9 @@ def split(s, beta_bits=0):
 
 
 @pytest.mark.parametrize("s", [3, 6, 9])
-def test_config4_size_mix_reduced(gpu, s):
+def test_size_mix_loguniform_reduced(gpu, s):
     """Log-uniform entries (1e-4..1e4, random signs), all six size classes, alpha=1, beta=0.5."""
-    b = synth.config4(count=150)
+    b = synth.size_mix_loguniform(count=150)
     C, plan = run_grouped(b, split(s))
     info = plan.info()
     assert info["slices"] == s and info["launches_per_call"] == 2
@@ -34,15 +34,15 @@ def test_config4_size_mix_reduced(gpu, s):
 
 
 @pytest.mark.parametrize("s", [3, 6, 9])
-def test_config3_uniform_reduced(gpu, s):
-    b = synth.config3(count=120)
+def test_size_mix_uniform_reduced(gpu, s):
+    b = synth.size_mix_uniform(count=120)
     C, _ = run_grouped(b, split(s))
     e = errors(b, host(C), oracle_batch(b))
     assert e.max() <= TOL_SPLIT[s], (s, e.max())
 
 
 def test_error_decreases_with_slices(gpu):
-    b = synth.config4(count=100)
+    b = synth.size_mix_loguniform(count=100)
     ref = oracle_batch(b)
     prev = np.inf
     for s in (2, 3, 4, 6, 8, 9):
@@ -55,7 +55,7 @@ def test_error_decreases_with_slices(gpu):
 
 def test_nine_slices_within_fp64_envelope(gpu):
     """9-slice error is of the order of the plain FP64 path's error."""
-    b = synth.config4(count=100)
+    b = synth.size_mix_loguniform(count=100)
     ref = oracle_batch(b)
     C64, _ = run_grouped(b)
     C9, _ = run_grouped(b, split(9))
@@ -111,8 +111,8 @@ def test_fixed_split_modes(gpu, dtype):
         assert e.max() <= TOL_SPLIT[s], (s, e.max())
 
 
-def test_config2_complex_split_reduced(gpu):
-    b = synth.config2(batch=64)
+def test_hermitian_unitary_split_reduced(gpu):
+    b = synth.hermitian_unitary_c128(batch=64)
     ref = oracle_batch(b)
     for s in (3, 6, 9):
         C = host(run_fixed(b, split(s)))
@@ -142,7 +142,7 @@ def test_split_ragged_shapes_and_zero_k(gpu, dtype):
 
 
 def test_split_alpha_zero_and_nan_c(gpu):
-    b = synth.config4(count=40)
+    b = synth.size_mix_loguniform(count=40)
     plan = bg.batched_gemm_plan("r64", b.table, split(6))
     An, Bn = dev(np.full_like(b.A, np.nan)), dev(np.full_like(b.B, np.nan))
     Cd = dev(b.C)
@@ -208,7 +208,7 @@ def test_bounded_wait_reports_timeout(gpu):
 
 
 def test_split_runs_leave_no_device_error(gpu):
-    b = synth.config4(count=30)
+    b = synth.size_mix_loguniform(count=30)
     run_grouped(b, split(9))
     bg.check_device_errors()
 

@@ -37,7 +37,7 @@ def _rank_main(rank, world, port, out_dir):
     w, r, _, pg = bench.dist_setup(Args())
     assert (w, r) == (world, rank) and pg is not None
     assert dist.get_backend() == "gloo"
-    batch, desc = bench.make_batch(4, 300, r)
+    batch, desc = bench.make_batch("mix-loguniform", 300, r)
     bench.barrier(pg)
     # rank r pretends its step took (r + 1) ms; every rank must see the slowest
     t_max = bench.max_over_ranks(pg, float(r + 1))

@@ -306,24 +306,24 @@ def test_shape_formula_sec3():
 
 
 def test_synth_config_shapes():
-    b1 = synth.config1()
+    b1 = synth.fixed_real_n32()
     assert b1.count == 64 and b1.fixed_shape() == (32, 32, 32, 64)
     assert np.all(np.abs(b1.A) <= 1.0)
-    b2 = synth.config2(batch=8)
+    b2 = synth.hermitian_unitary_c128(batch=8)
     for i in range(8):
         A = b2.instance(i, "A")
         assert np.array_equal(A, np.conj(A.T))
         U = b2.instance(i, "B")
         assert np.linalg.norm(np.conj(U.T) @ U - np.eye(64)) < 1e-13
-    b3 = synth.config3(count=300)
+    b3 = synth.size_mix_uniform(count=300)
     ns = b3.table[:, 0]
     assert set(np.unique(ns)).issubset(set(synth.CONFIG3_SIZES))
     assert np.all(b3.table[:, 6] % synth.ALIGN_ELEMS == 0)
-    b4 = synth.config4(count=50)
+    b4 = synth.size_mix_loguniform(count=50)
     mags = np.abs(b4.A[b4.A != 0])
     assert mags.min() >= 1e-4 * (1 - 1e-12) and mags.max() <= 1e4 * (1 + 1e-12)
     assert (b4.A < 0).any() and (b4.A > 0).any()
-    ch = synth.config5(walkers_small=3, walkers_large=1, n_small=8, n_large=16, steps=5,
+    ch = synth.annealing_chain(walkers_small=3, walkers_large=1, n_small=8, n_large=16, steps=5,
                        pool_small=4, pool_large=2)
     assert ch.idx.shape == (5, 4)
     assert ch.idx[:, :3].max() < 4 and ch.idx[:, 3].max() < 2

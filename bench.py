@@ -75,6 +75,8 @@ def parse_args():
     p.add_argument("--e2e-chunks", type=int, default=4, help="instance ranges of the e2e pipeline")
     p.add_argument("--no-library-baseline", action="store_true",
                    help="skip timing one cuBLAS DGEMM per instance (the paper's design)")
+    p.add_argument("--no-herk", action="store_true",
+                   help="skip the Hermitian-update line (rho = Psi Psi^H, Sec. 3 shapes)")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
 
@@ -332,6 +334,51 @@ def cublas_per_instance(batch, A, B, C0, steps: int, warmup: int, branches: int 
     graph.replay()
     torch.cuda.synchronize()
     return ms, C
+
+
+def herk_line(bg, steps: int, warmup: int, S: int = 17, count: int = 128):
+    """rho = Psi Psi^H of Sec. 3 for `count` complex states of S spins: Psi is
+    M x K with M = 2^(S - floor(S/2)), K = 2^floor(S/2); lower triangle through
+    plans with BG_PLAN_HERK, FP64 and 9 slices. Flops: 4 K M (M + 1) per
+    instance (the Hermitian half of 8 M M K)."""
+    import torch
+    from paper_2203_09353_gb300 import synth
+    M, K = 2 ** (S - S // 2), 2 ** (S // 2)
+    rng = np.random.default_rng(17)
+    table, la, lb, lc = synth.pack_table([(M, M, K)] * count)
+    A = torch.from_numpy(synth.complex_gaussian(rng, la)).cuda()
+    C0 = torch.zeros(lc, dtype=torch.complex128, device="cuda")
+    flops = count * 4.0 * K * M * (M + 1)
+    out, res = {}, {"workload": f"{count} complex Psi of {M} x {K} (S = {S}), C = Psi Psi^H",
+                    "gflop": flops / 1e9}
+    for mode in ("fp64", "split9"):
+        prec = None if mode == "fp64" else bg.precision("split", 9)
+        plan = bg.batched_gemm_plan("c128", table, prec, bg.BG_PLAN_HERK)
+        C = C0.clone()
+        for _ in range(max(1, warmup)):
+            bg.batched_gemm_grouped(plan, A, None, C, 1.0, 0.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            bg.batched_gemm_grouped(plan, A, None, C, 1.0, 0.0)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[mode] = {"ms_per_step": ms, "value": flops / (ms * 1e-3) / 1e12, "unit": UNIT}
+        out[mode] = C
+        plan.close()
+    # lower triangle of the 9-slice result against the FP64 one (normwise, max over instances)
+    worst = 0.0
+    for i in range(count):
+        co = int(table[i, 8])
+        # row-major views of column-major matrices: the lower triangle is the views' upper one
+        a = out["fp64"][co:co + M * M].view(M, M)
+        b = out["split9"][co:co + M * M].view(M, M)
+        d = torch.triu(a - b).abs().pow(2).sum().sqrt() / torch.triu(a).abs().pow(2).sum().sqrt()
+        worst = max(worst, float(d))
+    res["split9_vs_fp64_lower_rel"] = worst
+    return res
 
 
 def run_reference(args, world, rank, pg):
@@ -605,6 +652,11 @@ def main():
         log(f"cuBLAS per instance: {ms_l:.3f} ms/step")
         del C_l, ref64
 
+    herk = None
+    if not args.no_herk:
+        herk = herk_line(bg, steps=max(2, args.steps // 2), warmup=1)
+        log(f"Hermitian update: {json.dumps(herk)}")
+
     if rank != 0:
         return
     h = res[head]
@@ -628,6 +680,7 @@ def main():
         "modes": res,
         "fp64_peak_tflops_measured": fp64_peak,
         "library_baseline": lib_base,
+        "herk": herk,
         "peaks_source": pk_src,
     }
     print(json.dumps(line), flush=True)

@@ -104,8 +104,24 @@ enum {
   BG_PLAN_AUTOTUNE = 1u,      /* time candidate tile programs per size class and keep the fastest */
   BG_PLAN_USE_CACHE = 2u,     /* read/write autotune results in the JSON file cache_path */
   BG_PLAN_CAPTURE_GRAPH = 4u, /* batched_gemm_grouped replays a captured CUDA graph */
-  BG_PLAN_PROFILE = 8u        /* record CUDA events around each kernel (bg_plan_kernel_times) */
+  BG_PLAN_PROFILE = 8u,       /* record CUDA events around each kernel (bg_plan_kernel_times) */
+  BG_PLAN_HERK = 16u          /* Hermitian rank-k updates instead of Eq. (1), see below */
 };
+
+/* BG_PLAN_HERK. Sec. 3 builds the density matrix rho = Psi Psi^H of each
+ * state: a product of a matrix with its own conjugate transpose. A plan made
+ * with this flag computes, per instance,
+ *   C_i = alpha A_i A_i^H + beta C_i    (A_i A_i^T for real data),
+ * with A_i n x k (m_i must equal n_i). Conventions:
+ *  - The B fields of the table (ldb, b_off) and B_base are not used; B_base
+ *    may be NULL.
+ *  - alpha and beta must be real: a non-zero imaginary part is
+ *    BG_ERR_INVALID_ARG.
+ *  - Only the lower triangle of C_i, diagonal included, is read and
+ *    written. For complex128 the diagonal's imaginary parts are set to 0.
+ *  - Tiles wholly above the diagonal are not computed, which is about half
+ *    the work of the general product.
+ * Both precision modes support it; chain plans do not. */
 
 /* ---- Eq. (1), fixed-size batch -------------------------------------------
  * Sec. 2: the batch in which all instances have the same size and sit at a

@@ -28,6 +28,7 @@ LIB_PATH = os.path.join(HERE, "libbgemm.so")
 BG_R64, BG_C128 = 0, 1
 BG_MODE_FP64, BG_MODE_SPLIT_BF16 = 0, 1
 BG_PLAN_AUTOTUNE, BG_PLAN_USE_CACHE, BG_PLAN_CAPTURE_GRAPH, BG_PLAN_PROFILE = 1, 2, 4, 8
+BG_PLAN_HERK = 16  # Hermitian rank-k updates C = alpha A A^H + beta C (lower triangle)
 
 STATUS = {0: "BG_OK", 1: "BG_ERR_INVALID_ARG", 2: "BG_ERR_UNSUPPORTED", 3: "BG_ERR_CUDA",
           4: "BG_ERR_NOMEM", 5: "BG_ERR_CAPTURE", 6: "BG_ERR_TIMEOUT"}

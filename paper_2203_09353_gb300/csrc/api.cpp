@@ -139,16 +139,20 @@ static bg_status check_precision(const bg_precision* p, bg_precision* out) {
   return BG_OK;
 }
 
-static bg_status check_instance(const bg_instance& t, int64_t i) {
+// herk: a Hermitian rank-k update (m == n required, the B fields unused).
+static bg_status check_instance(const bg_instance& t, int64_t i, bool herk = false) {
   if (t.m < 0 || t.n < 0 || t.k < 0)
     return fail(BG_ERR_INVALID_ARG, "instance %lld: negative size", (long long)i);
   if (t.m > INT32_MAX / 2 || t.n > INT32_MAX / 2 || t.k > INT32_MAX / 2)
     return fail(BG_ERR_INVALID_ARG, "instance %lld: size too large", (long long)i);
-  if (t.lda < std::max<int64_t>(1, t.m) || t.ldb < std::max<int64_t>(1, t.k) ||
+  if (herk && t.m != t.n)
+    return fail(BG_ERR_INVALID_ARG, "instance %lld: a Hermitian update needs m == n",
+                (long long)i);
+  if (t.lda < std::max<int64_t>(1, t.m) || (!herk && t.ldb < std::max<int64_t>(1, t.k)) ||
       t.ldc < std::max<int64_t>(1, t.m))
     return fail(BG_ERR_INVALID_ARG, "instance %lld: leading dimension below the row count",
                 (long long)i);
-  if (t.a_off < 0 || t.b_off < 0 || t.c_off < 0)
+  if (t.a_off < 0 || (!herk && t.b_off < 0) || t.c_off < 0)
     return fail(BG_ERR_INVALID_ARG, "instance %lld: negative offset", (long long)i);
   return BG_OK;
 }
@@ -260,7 +264,7 @@ double item_cost(const WorkItem& w, const std::vector<int64_t>& mnk_k,
 // in `order`; items are sorted longest first.
 void build_items(const std::vector<int64_t>& ids, const std::vector<std::array<int64_t, 3>>& mnk,
                  const std::vector<int>& prog_of, std::vector<WorkItem>* items,
-                 std::vector<int32_t>* order) {
+                 std::vector<int32_t>* order, bool herk) {
   items->clear();
   order->clear();
   const size_t N = mnk.size();
@@ -281,6 +285,7 @@ void build_items(const std::vector<int64_t>& ids, const std::vector<std::array<i
       const int64_t m = mnk[id][0], n = mnk[id][1];
       for (int64_t c0 = 0; c0 < n; c0 += tn)
         for (int64_t r0 = 0; r0 < m; r0 += tm) {
+          if (herk && r0 + tm - 1 < c0) continue;  // wholly above the diagonal
           WorkItem w;
           w.inst = (int32_t)id;
           w.prog = (int16_t)p;
@@ -427,7 +432,7 @@ bg_status time_class_fp64(bg_plan* p, int cls, int prog, cudaStream_t st, double
   }
   std::vector<WorkItem> items;
   std::vector<int32_t> order;
-  build_items(sids, smnk, sprog, &items, &order);
+  build_items(sids, smnk, sprog, &items, &order, false);
   void *A = nullptr, *B = nullptr, *C = nullptr;
   int64_t* dt = nullptr;
   int32_t* dord = nullptr;
@@ -572,7 +577,7 @@ bg_status build_fp64_schedule(bg_plan* p, const char* cache_path, cudaStream_t s
     if (p->table[i].m > 0 && p->table[i].n > 0) live.push_back(i);
   std::vector<WorkItem> items;
   std::vector<int32_t> order;
-  build_items(live, mnk, prog_of, &items, &order);
+  build_items(live, mnk, prog_of, &items, &order, (p->flags & BG_PLAN_HERK) != 0);
   p->n_items = (int64_t)items.size();
   bg_status s;
   if ((s = upload(&p->d_order, order, &p->workspace_bytes)) != BG_OK) return s;
@@ -716,9 +721,10 @@ bg_status batched_gemm_plan(bg_plan** out, bg_dtype dtype, int64_t count,
   if (count < 0) return fail(BG_ERR_INVALID_ARG, "negative count");
   if (count > INT32_MAX / 2) return fail(BG_ERR_INVALID_ARG, "count too large");
   if (count > 0 && !host_table) return fail(BG_ERR_INVALID_ARG, "host_table is NULL");
-  if (flags & ~15u) return fail(BG_ERR_INVALID_ARG, "unknown plan flags 0x%x", flags);
+  if (flags & ~31u) return fail(BG_ERR_INVALID_ARG, "unknown plan flags 0x%x", flags);
+  const bool herk = (flags & BG_PLAN_HERK) != 0;
   for (int64_t i = 0; i < count; ++i)
-    if ((s = check_instance(host_table[i], i)) != BG_OK) return s;
+    if ((s = check_instance(host_table[i], i, herk)) != BG_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (stream_capturing(st))
     return fail(BG_ERR_CAPTURE, "batched_gemm_plan allocates; the stream is being captured");
@@ -747,7 +753,7 @@ bg_status batched_gemm_plan(bg_plan** out, bg_dtype dtype, int64_t count,
     p->launches_per_call = p->n_items > 0 ? 1 : 0;
   } else {
     s = split_plan_create(&p->split, dtype, pr, p->table, p->d_table, ctx->sms,
-                          (flags & BG_PLAN_AUTOTUNE) != 0, st, &g_last_error);
+                          (flags & BG_PLAN_AUTOTUNE) != 0, st, &g_last_error, herk);
     if (s != BG_OK) {
       destroy_plan(p);
       return s;
@@ -773,7 +779,7 @@ static bg_status run_grouped_direct(bg_plan* p, const void* A, const void* B, vo
   }
   if (p->prec.mode == BG_MODE_FP64) {
     cudaError_t e = launch_fp64_table(p->dtype, p->d_table, p->d_order, p->d_items, p->n_items, A,
-                                      B, C, sc, p->grid, st);
+                                      B, C, sc, p->grid, st, (p->flags & BG_PLAN_HERK) != 0);
     if (e != cudaSuccess) return cuda_fail(e, "grouped FP64 launch");
     if (ev) {
       BG_CUDA(cudaEventRecord(ev[1], st), "profiling event record");
@@ -796,7 +802,10 @@ bg_status batched_gemm_grouped(const bg_plan* plan, const void* A_base, const vo
   if (plan->count == 0) return BG_OK;
   if (!alpha || !beta) return fail(BG_ERR_INVALID_ARG, "alpha and beta must be host pointers");
   const Scalars sc = make_scalars(plan->dtype, alpha, beta);
-  if (!C_base || (!sc.alpha_zero && (!A_base || !B_base)))
+  const bool herk = (plan->flags & BG_PLAN_HERK) != 0;
+  if (herk && (sc.alpha_im != 0.0 || sc.beta_im != 0.0))
+    return fail(BG_ERR_INVALID_ARG, "a Hermitian update takes real alpha and beta");
+  if (!C_base || (!sc.alpha_zero && (!A_base || (!herk && !B_base))))
     return fail(BG_ERR_INVALID_ARG, "null base pointer");
   if (!aligned(C_base, plan->dtype) || (A_base && !aligned(A_base, plan->dtype)) ||
       (B_base && !aligned(B_base, plan->dtype)))

@@ -59,10 +59,12 @@ cudaError_t launch_fp64_fixed(bg_dtype dt, int prog, int64_t m, int64_t n, int64
                               const void* B, int64_t ldb, int64_t sB, void* C, int64_t ldc,
                               int64_t sC, int64_t batch, int grid_cap, cudaStream_t st);
 
+// herm: the plan's instances are Hermitian rank-k updates (B = A^H, lower
+// triangle stored).
 cudaError_t launch_fp64_table(bg_dtype dt, const int64_t* d_table, const int32_t* d_order,
                               const WorkItem* d_items, int64_t n_items, const void* A,
                               const void* B, void* C, const Scalars& s, int grid,
-                              cudaStream_t st);
+                              cudaStream_t st, bool herm = false);
 
 cudaError_t launch_fp64_chain(bg_dtype dt, const int64_t* d_wn, const int64_t* d_woff,
                               const int64_t* d_pool_off, const int64_t* d_pool_n,

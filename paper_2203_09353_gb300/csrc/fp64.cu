@@ -25,7 +25,29 @@ struct Desc {
   double* C;
   int m, n, k;
   int64_t lda, ldb, ldc;  // elements
+  // Hermitian rank-k update (Sec. 3, rho = Psi Psi^H): B is A^H (A^T when
+  // real), read from A; only outputs on or below the diagonal are stored,
+  // and a complex diagonal gets a zero imaginary part.
+  int herm;
 };
+
+// Element (p, c) of B (real).
+__device__ __forceinline__ double ld_b(const Desc& d, int p, int c) {
+  return d.herm ? __ldg(d.A + c + (int64_t)p * d.lda) : __ldg(d.B + p + (int64_t)c * d.ldb);
+}
+
+// Element (p, c) of B (complex).
+__device__ __forceinline__ double2 ld_bc(const Desc& d, int p, int c) {
+  if (d.herm) {
+    double2 v = __ldg(reinterpret_cast<const double2*>(d.A) + c + (int64_t)p * d.lda);
+    v.y = -v.y;
+    return v;
+  }
+  return __ldg(reinterpret_cast<const double2*>(d.B) + p + (int64_t)c * d.ldb);
+}
+
+// Whether output (r, c) is stored (Hermitian updates keep the lower triangle).
+__device__ __forceinline__ bool keep_out(const Desc& d, int r, int c) { return !d.herm || r >= c; }
 
 // Fixed-size batch: instance i at constant strides.
 struct FixedSrc {
@@ -42,6 +64,7 @@ struct FixedSrc {
     d.C = C + i * sC * esz;
     d.m = m; d.n = n; d.k = k;
     d.lda = lda; d.ldb = ldb; d.ldc = ldc;
+    d.herm = 0;
     return d;
   }
   __device__ int64_t small_inst(int64_t pos) const { return pos; }
@@ -55,14 +78,16 @@ struct TableSrc {
   const double* B;
   double* C;
   int esz;
+  int herm;  // plan of Hermitian rank-k updates (B unused)
   __device__ Desc desc(int64_t i) const {
     const int64_t* t = table + 9 * i;
     Desc d;
     d.m = (int)t[0]; d.n = (int)t[1]; d.k = (int)t[2];
     d.lda = t[3]; d.ldb = t[4]; d.ldc = t[5];
     d.A = A + t[6] * esz;
-    d.B = B + t[7] * esz;
+    d.B = herm ? d.A : B + t[7] * esz;
     d.C = C + t[8] * esz;
+    d.herm = herm;
     return d;
   }
   __device__ int64_t small_inst(int64_t pos) const { return order[pos]; }
@@ -94,6 +119,7 @@ struct ChainSrc {
     d.A = U + (ok ? pool_off[j] : 0) * esz;
     d.B = Cin + woff[w] * esz;
     d.C = Cout + woff[w] * esz;
+    d.herm = 0;
     return d;
   }
   __device__ int64_t small_inst(int64_t pos) const { return order[pos]; }
@@ -160,7 +186,7 @@ __device__ __forceinline__ void tile_r64(const Desc& d, int r0, int c0, const Sc
       const int r = r0 + ar, kk = k0 + ak + 4 * j;
       ra[j] = (r < d.m && kk < K) ? __ldg(d.A + r + (int64_t)kk * d.lda) : 0.0;
       const int kb = k0 + bk, c = c0 + bc + 16 * j;
-      rb[j] = (kb < K && c < d.n) ? __ldg(d.B + kb + (int64_t)c * d.ldb) : 0.0;
+      rb[j] = (kb < K && c < d.n) ? ld_b(d, kb, c) : 0.0;
     }
   };
   auto sstore = [&](int st) {
@@ -205,7 +231,7 @@ __device__ __forceinline__ void tile_r64(const Desc& d, int r0, int c0, const Sc
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = r0 + ty * 4 + i;
-      if (r >= d.m) continue;
+      if (r >= d.m || !keep_out(d, r, c)) continue;
       double* cp = d.C + r + (int64_t)c * d.ldc;
       double v = s.alpha_re * acc[i][j];
       if (!s.beta_zero) v = fma(s.beta_re, *cp, v);
@@ -247,7 +273,7 @@ __device__ __forceinline__ void tile_r64_dmma(const Desc& d, int r0, int c0, con
       const int r = r0 + ar, kk = k0 + ak + 4 * j;
       ra[j] = (r < d.m && kk < K) ? __ldg(d.A + r + (int64_t)kk * d.lda) : 0.0;
       const int kb = k0 + bk, c = c0 + bc + 16 * j;
-      rb[j] = (kb < K && c < d.n) ? __ldg(d.B + kb + (int64_t)c * d.ldb) : 0.0;
+      rb[j] = (kb < K && c < d.n) ? ld_b(d, kb, c) : 0.0;
     }
   };
   auto sstore = [&](int st) {
@@ -291,7 +317,7 @@ __device__ __forceinline__ void tile_r64_dmma(const Desc& d, int r0, int c0, con
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = c0 + wn * 16 + j * 8 + 2 * t + h;
-        if (c >= d.n) continue;
+        if (c >= d.n || !keep_out(d, r, c)) continue;
         double* cp = d.C + r + (int64_t)c * d.ldc;
         double v = s.alpha_re * acc[i][j][h];
         if (!s.beta_zero) v = fma(s.beta_re, *cp, v);
@@ -334,7 +360,6 @@ __device__ __forceinline__ void tile_c128(const Desc& d, int r0, int c0, const S
   const int tx = tid & 15, ty = tid >> 4;
   const int K = s.alpha_zero ? 0 : d.k;
   const double2* A = reinterpret_cast<const double2*>(d.A);
-  const double2* B = reinterpret_cast<const double2*>(d.B);
   double2 acc[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -351,7 +376,7 @@ __device__ __forceinline__ void tile_c128(const Desc& d, int r0, int c0, const S
       const int r = r0 + ar, kk = k0 + ak + 8 * j;
       ra[j] = (r < d.m && kk < K) ? __ldg(A + r + (int64_t)kk * d.lda) : z;
       const int kb = k0 + bk, c = c0 + bc + 16 * j;
-      rb[j] = (kb < K && c < d.n) ? __ldg(B + kb + (int64_t)c * d.ldb) : z;
+      rb[j] = (kb < K && c < d.n) ? ld_bc(d, kb, c) : z;
     }
   };
   auto sstore = [&](int st) {
@@ -391,9 +416,11 @@ __device__ __forceinline__ void tile_c128(const Desc& d, int r0, int c0, const S
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       const int r = r0 + ty * 2 + i;
-      if (r >= d.m) continue;
+      if (r >= d.m || !keep_out(d, r, c)) continue;
       double2* cp = C + r + (int64_t)c * d.ldc;
-      *cp = c_epilogue(acc[i][j], cp, s);
+      double2 v = c_epilogue(acc[i][j], cp, s);
+      if (d.herm && r == c) v.y = 0.0;
+      *cp = v;
     }
   }
 }
@@ -421,12 +448,13 @@ __device__ __forceinline__ void small_r64(const Desc& d, const Scalars& s) {
       const double a = __ldg(ap + (int64_t)p * d.lda);
 #pragma unroll
       for (int j = 0; j < MAXOUT; ++j)
-        if (c0 + j * cstep < n) acc[j] = fma(a, __ldg(bp + p + j * bstep), acc[j]);
+        if (c0 + j * cstep < n)
+          acc[j] = fma(a, d.herm ? ld_b(d, p, c0 + j * cstep) : __ldg(bp + p + j * bstep), acc[j]);
     }
 #pragma unroll
     for (int j = 0; j < MAXOUT; ++j) {
       const int c = c0 + j * cstep;
-      if (c < n) {
+      if (c < n && keep_out(d, r, c)) {
         double* cp = d.C + r + (int64_t)c * d.ldc;
         double v = s.alpha_re * acc[j];
         if (!s.beta_zero) v = fma(s.beta_re, *cp, v);
@@ -440,8 +468,7 @@ __device__ __forceinline__ void small_r64(const Desc& d, const Scalars& s) {
         const int o = lane + 32 * j;
         if (o < mn) {
           const int r = o % m, c = o / m;
-          acc[j] = fma(__ldg(d.A + r + (int64_t)p * d.lda), __ldg(d.B + p + (int64_t)c * d.ldb),
-                       acc[j]);
+          acc[j] = fma(__ldg(d.A + r + (int64_t)p * d.lda), ld_b(d, p, c), acc[j]);
         }
       }
     }
@@ -450,6 +477,7 @@ __device__ __forceinline__ void small_r64(const Desc& d, const Scalars& s) {
       const int o = lane + 32 * j;
       if (o < mn) {
         const int r = o % m, c = o / m;
+        if (!keep_out(d, r, c)) continue;
         double* cp = d.C + r + (int64_t)c * d.ldc;
         double v = s.alpha_re * acc[j];
         if (!s.beta_zero) v = fma(s.beta_re, *cp, v);
@@ -478,14 +506,17 @@ __device__ __forceinline__ void small_c128(const Desc& d, const Scalars& s) {
       const double2 a = __ldg(A + r + (int64_t)p * d.lda);
 #pragma unroll
       for (int j = 0; j < MAXOUT; ++j)
-        if (c0 + j * cstep < n) cmac(acc[j], a, __ldg(bp + p + j * bstep));
+        if (c0 + j * cstep < n)
+          cmac(acc[j], a, d.herm ? ld_bc(d, p, c0 + j * cstep) : __ldg(bp + p + j * bstep));
     }
 #pragma unroll
     for (int j = 0; j < MAXOUT; ++j) {
       const int c = c0 + j * cstep;
-      if (c < n) {
+      if (c < n && keep_out(d, r, c)) {
         double2* cp = C + r + (int64_t)c * d.ldc;
-        *cp = c_epilogue(acc[j], cp, s);
+        double2 v = c_epilogue(acc[j], cp, s);
+        if (d.herm && r == c) v.y = 0.0;
+        *cp = v;
       }
     }
   } else {
@@ -495,7 +526,7 @@ __device__ __forceinline__ void small_c128(const Desc& d, const Scalars& s) {
         const int o = lane + 32 * j;
         if (o < mn) {
           const int r = o % m, c = o / m;
-          cmac(acc[j], __ldg(A + r + (int64_t)p * d.lda), __ldg(B + p + (int64_t)c * d.ldb));
+          cmac(acc[j], __ldg(A + r + (int64_t)p * d.lda), ld_bc(d, p, c));
         }
       }
     }
@@ -504,8 +535,11 @@ __device__ __forceinline__ void small_c128(const Desc& d, const Scalars& s) {
       const int o = lane + 32 * j;
       if (o < mn) {
         const int r = o % m, c = o / m;
+        if (!keep_out(d, r, c)) continue;
         double2* cp = C + r + (int64_t)c * d.ldc;
-        *cp = c_epilogue(acc[j], cp, s);
+        double2 v = c_epilogue(acc[j], cp, s);
+        if (d.herm && r == c) v.y = 0.0;
+        *cp = v;
       }
     }
   }
@@ -649,9 +683,10 @@ cudaError_t launch_fp64_fixed(bg_dtype dt, int prog, int64_t m, int64_t n, int64
 cudaError_t launch_fp64_table(bg_dtype dt, const int64_t* d_table, const int32_t* d_order,
                               const WorkItem* d_items, int64_t n_items, const void* A,
                               const void* B, void* C, const Scalars& s, int grid,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool herm) {
   if (n_items <= 0) return cudaSuccess;
   TableSrc src;
+  src.herm = herm ? 1 : 0;
   src.table = d_table;
   src.order = d_order;
   src.A = static_cast<const double*>(A);

@@ -89,6 +89,12 @@ __device__ __forceinline__ void load8(const SliceArgs& a, bool isA, const SInst&
     for (int u = 0; u < 8; ++u) x[u] = 0.0;
     return;
   }
+  if (!isA && a.herk) {
+    // Hermitian update: column j of B = A^H is row j of A conjugated, which in
+    // the real view is row 2j of A's 2 x 2 expansion (re, -im); real: row j
+    isA = true;
+    line = a.cplx ? 2 * line : line;
+  }
   if (isA) {
     if (!a.cplx) {
       const double* p = a.A + in.a_off + line + (int64_t)q0 * in.lda;
@@ -338,6 +344,7 @@ struct SplitPlan {
   int s = 0, beta = 0, bn = 0, kpass = 0, a_stages = 0;
   size_t smem = 0;
   bool chain = false;
+  bool herk = false;       // Hermitian rank-k updates (B = A^H, lower triangle)
   int sms = 0;
   int64_t count = 0;
   // device
@@ -555,6 +562,10 @@ static void make_tables(const SplitPlan* p, const std::vector<bg_instance>& tabl
         // row blocks inner: the units sharing a B block run side by side (L2 reuse)
         for (int64_t cb = 0; cb < cbs; ++cb)
           for (int64_t rb = 0; rb < rbs; ++rb) {
+            // Hermitian update: a tile wholly above the diagonal (its last row,
+            // counted in complex rows, before its first column) is not needed
+            if (p->herk && ((std::min<int64_t>(mv, (rb + 1) * BM) - 1) >> (cplx ? 1 : 0)) < cb * BN)
+              continue;
             SplitUnit U{};
             U.a_tile0 = tA0 + rb * s * nkb;
             U.b_tile0 = tB0 + cb * s * nkb;
@@ -668,7 +679,8 @@ static void grids(SplitPlan* p) {
 
 bg_status split_plan_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr,
                             const std::vector<bg_instance>& table, const int64_t* d_table,
-                            int sms, bool autotune, cudaStream_t st, std::string* err) {
+                            int sms, bool autotune, cudaStream_t st, std::string* err,
+                            bool herk) {
   (void)d_table;
   (void)autotune;
   (void)st;
@@ -677,6 +689,7 @@ bg_status split_plan_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr
     delete p;
     return BG_ERR_INVALID_ARG;
   }
+  p->herk = herk;
   bg_status s = build_instances(p, table, err);
   if (s != BG_OK) {
     split_plan_destroy(p);
@@ -710,6 +723,7 @@ static cudaError_t launch_slicer(SplitPlan* p, const SliceJob* jobs, int64_t njo
   a.s = p->s;
   a.beta = p->beta;
   a.bn = p->bn;
+  a.herk = p->herk ? 1 : 0;
   const int grid = (int)std::min<int64_t>(p->grid_slice, njobs);
   // compile-time (slices, digit width) versions for the documented modes
   if (p->s == 3 && p->beta == 7) {
@@ -752,6 +766,7 @@ static cudaError_t launch_gemm(SplitPlan* p, void* C, const Scalars& sc, const i
   g.s = p->s;
   g.beta = p->beta;
   g.skip_product = sc.alpha_zero;
+  g.herk = p->herk ? 1 : 0;
   g.kpass = p->kpass;
   g.a_stages = p->a_stages;
   g.err = d_err;

@@ -28,7 +28,7 @@ int split_default_beta(int slices);
 
 bg_status split_plan_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr,
                             const std::vector<bg_instance>& table, const int64_t* d_table,
-                            int sms, bool autotune, cudaStream_t st, std::string* err);
+                            int sms, bool autotune, cudaStream_t st, std::string* err, bool herk = false);
 bg_status split_chain_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr,
                              const std::vector<int64_t>& wn, const std::vector<int64_t>& woff,
                              const std::vector<int64_t>& pool_n,

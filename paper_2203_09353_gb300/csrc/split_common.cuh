@@ -86,6 +86,7 @@ struct SliceArgs {
   int32_t* metaA;
   int32_t* metaB;
   int cplx, s, beta, bn;
+  int herk;  // Hermitian update: B lines are rows of A (conjugated), read through the A side
 };
 
 struct GemmArgs {
@@ -107,6 +108,7 @@ struct GemmArgs {
   int cplx, s, beta, skip_product;
   int kpass;                  // k-blocks per exact pass
   int a_stages;               // slots of the A ring
+  int herk;                   // Hermitian update: store only the lower triangle
   int* err;
 };
 

@@ -16,7 +16,8 @@ template <bool CPLX, bool FASTCONV>
 __device__ __forceinline__ void epi_store8(const GemmArgs& g, const long long (&acc)[8],
                                            const int32_t* mb, int colb, bool rvalid, int cmin,
                                            int cmax, int coff, int64_t cbase, int64_t ldcv,
-                                           int Ebase, bool first_pass, bool alpha_one, int rr) {
+                                           int Ebase, bool first_pass, bool alpha_one, int rr,
+                                           int dcol) {
   const bool need_c = !first_pass || !g.sc.beta_zero;
   double cv[8];
   int fj[8];
@@ -62,6 +63,7 @@ __device__ __forceinline__ void epi_store8(const GemmArgs& g, const long long (&
         double v = fma(g.sc.alpha_re, x, sgn * g.sc.alpha_im * xp);
         if (!first_pass) v += cv[j];
         else if (!g.sc.beta_zero) v = fma(g.sc.beta_re, cv[j], fma(sgn * g.sc.beta_im, cpn, v));
+        if (col == dcol) v = 0.0;  // Hermitian update: real diagonal
         *cp = v;
       }
     }
@@ -318,6 +320,15 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
       const int mv = CPLX ? 2 * in.m : in.m;
       rvalid = rvalid && rr < mv;
       if (U.g == 1) cmax = min(cmax, in.n - U.c0);
+      // Hermitian update: only columns up to the diagonal (instance row >=
+      // instance column, in complex rows for complex data); the diagonal of
+      // complex data is real
+      int dcol = -1;
+      if (g.herk) {
+        const int row_inst = CPLX ? rr >> 1 : rr;
+        cmax = min(cmax, row_inst - coff + 1);
+        if (CPLX && (rr & 1)) dcol = row_inst - coff;
+      }
       const int64_t cbase = (CPLX ? 2 * in.c_off : in.c_off) + rr;
       const int64_t ldcv = CPLX ? 2 * in.ldc : in.ldc;
       const int Ebase = F - 62 + e_i - 2 * g.beta;
@@ -376,7 +387,7 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
               }
             }
             epi_store8<CPLX, kFastConv>(g, acc, mb, col0 + j0, rvalid, cmin, cmax, coff, cbase, ldcv, Ebase,
-                             c == 0, alpha_one, rr);
+                             c == 0, alpha_one, rr, dcol);
           }
           if (npass > 0) {
             tc_fence_before();
@@ -442,7 +453,7 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
           // ---- exact conversion, alpha/beta, store (TMEM already free: overlaps the next MMAs).
           for (int j0 = 0; j0 < COLS; j0 += 8) {
             epi_store8<CPLX, kFastConv>(g, *reinterpret_cast<const long long(*)[8]>(acc), mb, col0 + j0,
-                             rvalid, cmin, cmax, coff, cbase, ldcv, Ebase, c == 0, alpha_one, rr);
+                             rvalid, cmin, cmax, coff, cbase, ldcv, Ebase, c == 0, alpha_one, rr, dcol);
             // rotate the next 8 accumulators into place (keeps the loop body small)
 #pragma unroll
             for (int j = 0; j + 8 < COLS; ++j) acc[j] = acc[j + 8];

@@ -243,6 +243,32 @@ def log(msg: str) -> None:
     sys.stderr.flush()
 
 
+def bind_near_gpu(local: int) -> str:
+    """Pins this process to the CPU cores next to its GPU (the PCI device's
+    local_cpulist), so that the pinned host buffers of the end-to-end step are
+    allocated on the memory node wired to that GPU. Returns what was done."""
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout.split()
+        if not out:
+            return "unbound (no bus id)"
+        bus = out[min(local, len(out) - 1)].strip().lower()
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}/local_cpulist"
+        cpus = set()
+        with open(path) as fh:
+            for part in fh.read().strip().split(","):
+                lo, _, hi = part.partition("-")
+                cpus.update(range(int(lo), int(hi or lo) + 1))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return "unbound (no local cores available)"
+        os.sched_setaffinity(0, cpus)
+        return f"bound to {len(cpus)} cores local to GPU {bus}"
+    except Exception as e:  # the binding is an optimisation only
+        return f"unbound ({type(e).__name__})"
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -426,6 +452,7 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
     torch.cuda.set_device(local)
+    log(bind_near_gpu(local))
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     pk, pk_src = peaks()

@@ -77,6 +77,8 @@ def parse_args():
                    help="skip timing one cuBLAS DGEMM per instance (the paper's design)")
     p.add_argument("--no-herk", action="store_true",
                    help="skip the Hermitian-update line (rho = Psi Psi^H, Sec. 3 shapes)")
+    p.add_argument("--no-chain", action="store_true",
+                   help="skip the chained-product line (1024 walkers, Alg. 1 step loop)")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
 
@@ -407,6 +409,48 @@ def herk_line(bg, steps: int, warmup: int, S: int = 17, count: int = 128):
     return res
 
 
+def chain_line(bg, fp64_steps: int = 10, split_steps: int = 200):
+    """The annealing-shaped chain: 960 complex walkers of n = 256 and 64 of
+    n = 1024, each multiplied by a pool unitary per step (Alg. 1 step loop),
+    through chain_step with the step loop captured in a CUDA graph. 9 slices
+    run all 200 steps; FP64, 50 times slower, a bounded number. The unitarity
+    drift ||C^H C - I||_F of every walker is reported after the last step."""
+    import torch
+    from paper_2203_09353_gb300 import synth
+    ch = synth.annealing_chain()
+    pool, pn, po, states, wo, gidx = synth.chain_layout(ch)
+    dpool = torch.from_numpy(pool).cuda()
+    didx = torch.from_numpy(gidx).cuda()
+    dn = torch.from_numpy(ch.n_walker.astype(np.int64)).cuda()
+    do = torch.from_numpy(wo).cuda()
+    step_flops = float(np.sum(8.0 * ch.n_walker.astype(np.float64) ** 3))
+    res = {"workload": f"{ch.walkers} complex walkers (960 x n=256, 64 x n=1024), pool of "
+                       f"{len(pn)} Haar unitaries, C <- U_t C", "gflop_per_step": step_flops / 1e9}
+    for mode, steps in (("fp64", fp64_steps), ("split9", split_steps)):
+        prec = None if mode == "fp64" else bg.precision("split", 9)
+        plan = bg.chain_plan("c128", ch.n_walker, wo, pn, po, prec, bg.BG_PLAN_CAPTURE_GRAPH)
+        ping = torch.from_numpy(states).cuda()
+        pong = torch.empty_like(ping)
+        # warm-up with the timed arguments: captures the step loop's graph
+        bg.chain_step(plan, dpool, didx[:steps], ping, pong, steps)
+        ping.copy_(torch.from_numpy(states))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bg.chain_step(plan, dpool, didx[:steps], ping, pong, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out = ping if steps % 2 == 0 else pong
+        drift = torch.zeros(ch.walkers, dtype=torch.float64, device="cuda")
+        bg.unitarity_drift("c128", dn, do, out, drift, ch.walkers)
+        res[mode] = {"steps": steps, "ms": ms, "ms_per_step": ms / steps,
+                     "value": step_flops * steps / (ms * 1e-3) / 1e12, "unit": UNIT,
+                     "max_unitarity_drift": float(drift.max())}
+        plan.close()
+    return res
+
+
 def run_reference(args, world, rank, pg):
     """--impl reference: the CPU oracle, as it stands, on bounded samples of the workload."""
     if rank != 0:
@@ -679,6 +723,11 @@ def main():
         log(f"cuBLAS per instance: {ms_l:.3f} ms/step")
         del C_l, ref64
 
+    chain = None
+    if not args.no_chain:
+        chain = chain_line(bg)
+        log(f"chain: {json.dumps(chain)}")
+
     herk = None
     if not args.no_herk:
         herk = herk_line(bg, steps=max(2, args.steps // 2), warmup=1)
@@ -708,6 +757,7 @@ def main():
         "fp64_peak_tflops_measured": fp64_peak,
         "library_baseline": lib_base,
         "herk": herk,
+        "chain": chain,
         "peaks_source": pk_src,
     }
     print(json.dumps(line), flush=True)

@@ -299,3 +299,31 @@ def annealing_chain(walkers_small: int = 960, walkers_large: int = 64, n_small: 
     if walkers_large:
         C0 += list(haar_unitary(rng, n_large, walkers_large))
     return Chain(nw, pools, idx, C0)
+
+
+def chain_layout(chain: Chain):
+    """Packs a chain for chain_plan / chain_step: the pool (all sizes, column-major,
+    back to back) with each entry's size and offset, the walkers' start states
+    with their offsets, and the [steps, walkers] table of global pool indices.
+    Returns (pool, pool_n, pool_off, states, state_off, gidx)."""
+    sizes = sorted(chain.pools)
+    pool_n, pool_off, chunks, base = [], [], [], {}
+    off = 0
+    for n in sizes:
+        base[n] = len(pool_n)
+        for U in chain.pools[n]:
+            pool_n.append(n)
+            pool_off.append(off)
+            chunks.append(np.asfortranarray(U).ravel(order="F"))
+            off += n * n
+    state_off, st = [], []
+    off = 0
+    for C in chain.C0:
+        state_off.append(off)
+        st.append(np.asfortranarray(C).ravel(order="F"))
+        off += C.shape[0] ** 2
+    first = np.array([base[int(n)] for n in chain.n_walker], dtype=np.int64)
+    gidx = (chain.idx.astype(np.int64) + first[None, :]).astype(np.int32)
+    return (np.concatenate(chunks), np.array(pool_n, dtype=np.int64),
+            np.array(pool_off, dtype=np.int64), np.concatenate(st),
+            np.array(state_off, dtype=np.int64), gidx)

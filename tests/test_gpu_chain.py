@@ -13,30 +13,8 @@ pytestmark = pytest.mark.gpu
 
 
 def layout(chain):
-    """Pack pool and states column-major; returns (pool flat, pool_n, pool_off, states, w_off)."""
-    sizes = sorted(chain.pools)
-    pool_n, pool_off, chunks = [], [], []
-    base = {}
-    off = 0
-    for n in sizes:
-        base[n] = len(pool_n)
-        for U in chain.pools[n]:
-            pool_n.append(n)
-            pool_off.append(off)
-            chunks.append(np.asfortranarray(U).ravel(order="F"))
-            off += n * n
-    pool = np.concatenate(chunks)
-    w_off, st = [], []
-    off = 0
-    for C in chain.C0:
-        w_off.append(off)
-        st.append(np.asfortranarray(C).ravel(order="F"))
-        off += C.shape[0] ** 2
-    states = np.concatenate(st)
-    # global pool index per (step, walker)
-    gidx = np.array([[base[int(chain.n_walker[w])] + chain.idx[t, w]
-                      for w in range(chain.walkers)] for t in range(chain.steps)], dtype=np.int32)
-    return pool, np.array(pool_n), np.array(pool_off), states, np.array(w_off), gidx
+    """Pool, pool sizes and offsets, states, state offsets, global pool indices."""
+    return synth.chain_layout(chain)
 
 
 def oracle_chain(chain, steps):

@@ -75,48 +75,166 @@ namespace {
 // Work distribution: the (group of 4 lines) x (k-block) items of a block are
 // dealt to the CTA's warps; a warp covers 4 lines x 8 chunks of 8 k values,
 // so each plane store writes 4 whole 128-byte rows (512 contiguous bytes)
-// and every lane keeps 8 loads in flight. Line maxima and norm sums meet in
+// and every lane keeps 8 values in flight. Line maxima and norm sums meet in
 // shared memory through integer atomics (max, and sums of fixed-point
 // squares), so the result does not depend on the order of the items.
 
-// The 8 values x[u] = line `line`, k = q0 + u of the block's operand (A rows
-// or B columns; complex A through its 2 x 2 real expansion), 0 beyond k' or
-// for an invalid line.
-__device__ __forceinline__ void load8(const SliceArgs& a, bool isA, const SInst& in, bool valid,
-                                      int line, int q0, int kv, double (&x)[8]) {
-  if (!valid) {
+// Where line l of a job's block starts in its operand, and how far apart its
+// consecutive k' values lie; built once per job in shared memory.
+//   rows of A, real:    x(k') = A[off + k' ld]
+//   rows of A, complex: z = A[off + (k' / 2) ld] in double2 units; row 2r of
+//                       the 2 x 2 expansion reads (re, -im), row 2r+1 (im, re)
+//   columns of B:       x(k') = B[off + k'] (complex: re, im interleaved)
+// off < 0 marks a line beyond its instance. ldx = 2 ld + (odd complex row).
+struct LineSrc {
+  int64_t off, ldx;
+};
+
+__device__ __forceinline__ LineSrc line_src(const SliceArgs& a, const SliceJob& J, bool isA,
+                                            int l) {
+  LineSrc r{-1, 0};
+  const int li = l / J.span;
+  const int line = J.org + l % J.span;
+  if (li >= J.g) return r;
+  const SInst in = isA ? a.instA[a.orderA[J.pos + li]] : a.instB[a.orderB[J.pos + li]];
+  if (!(isA ? line < (a.cplx ? 2 * in.m : in.m) : line < in.n)) return r;
+  if (isA || a.herk) {
+    // Hermitian update, B side: column j of B = A^H is row j of A conjugated,
+    // which in the real view is row 2j of A's 2 x 2 expansion (re, -im)
+    const int row = isA ? line : (a.cplx ? 2 * line : line);
+    r.off = a.cplx ? in.a_off + (row >> 1) : in.a_off + row;
+    r.ldx = 2 * in.lda + (a.cplx ? (row & 1) : 0);
+  } else {
+    r.off = a.cplx ? 2 * in.b_off + (int64_t)line * 2 * in.ldb : in.b_off + (int64_t)line * in.ldb;
+    r.ldx = 2;
+  }
+  return r;
+}
+
+// The 8 values x[u] = (line, k' = q0 + u) of the block's operand, 0 beyond
+// k' or for a line beyond its instance; rows: the lines are rows of A.
+__device__ __forceinline__ void load8(const SliceArgs& a, bool rows, LineSrc src, int q0, int kv,
+                                      double (&x)[8]) {
+  if (src.off < 0) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) x[u] = 0.0;
     return;
   }
-  if (!isA && a.herk) {
-    // Hermitian update: column j of B = A^H is row j of A conjugated, which in
-    // the real view is row 2j of A's 2 x 2 expansion (re, -im); real: row j
-    isA = true;
-    line = a.cplx ? 2 * line : line;
-  }
-  if (isA) {
+  const int64_t ld = src.ldx >> 1;
+  if (rows) {
     if (!a.cplx) {
-      const double* p = a.A + in.a_off + line + (int64_t)q0 * in.lda;
+      const double* p = a.A + src.off + (int64_t)q0 * ld;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) x[u] = q0 + u < kv ? __ldg(p + (int64_t)u * in.lda) : 0.0;
+      for (int u = 0; u < 8; ++u) x[u] = q0 + u < kv ? __ldg(p + (int64_t)u * ld) : 0.0;
     } else {
-      const double2* p = reinterpret_cast<const double2*>(a.A) + in.a_off + (line >> 1) +
-                         (int64_t)(q0 >> 1) * in.lda;
-      const bool im_row = line & 1;
+      const double2* p = reinterpret_cast<const double2*>(a.A) + src.off + (int64_t)(q0 >> 1) * ld;
+      const bool im_row = src.ldx & 1;
 #pragma unroll
       for (int u = 0; u < 8; u += 2) {
-        const double2 z = q0 + u < kv ? __ldg(p + (int64_t)(u >> 1) * in.lda) : make_double2(0.0, 0.0);
-        // row 2r: (re, -im); row 2r+1: (im, re)
+        const double2 z = q0 + u < kv ? __ldg(p + (int64_t)(u >> 1) * ld) : make_double2(0.0, 0.0);
         x[u] = im_row ? z.y : z.x;
         x[u + 1] = q0 + u + 1 < kv ? (im_row ? z.x : -z.y) : 0.0;
       }
     }
   } else {
-    const double* p = a.cplx ? a.B + 2 * in.b_off + q0 + (int64_t)line * 2 * in.ldb
-                             : a.B + in.b_off + q0 + (int64_t)line * in.ldb;
+    const double* p = a.B + src.off + q0;
+    // 16-byte loads where the column allows them (a real B with an odd ldb or
+    // offset puts every other column on an 8-byte boundary)
+    const bool vec = (reinterpret_cast<uintptr_t>(p) & 15) == 0;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) x[u] = q0 + u < kv ? __ldg(p + u) : 0.0;
+    for (int u = 0; u < 8; u += 2) {
+      if (vec && q0 + u + 1 < kv) {
+        const double2 z = __ldg(reinterpret_cast<const double2*>(p + u));
+        x[u] = z.x;
+        x[u + 1] = z.y;
+      } else {
+        x[u] = q0 + u < kv ? __ldg(p + u) : 0.0;
+        x[u + 1] = q0 + u + 1 < kv ? __ldg(p + u + 1) : 0.0;
+      }
+    }
+  }
+}
+
+// Line maximum of the 8 values of a lane, merged over the 8 lanes of the line
+// and into s_max.
+__device__ __forceinline__ void merge_max(const double (&x)[8], int cc, unsigned long long* s_max_l) {
+  unsigned long long mx = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x[u]) & 0x7FFFFFFFFFFFFFFFull;
+    mx = b > mx ? b : mx;
+  }
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if (cc == 0 && mx) atomicMax(s_max_l, mx);
+}
+
+// Digit planes of the 8 values of a lane (chunk cc of a line with exponent e),
+// stored at dst (plane p at dst + p tile_bytes); the line's sum of squared
+// absolute digit weights is merged into s_n2.
+template <int S, int BETA>
+__device__ __forceinline__ void cut_item(const double (&x)[8], int e, const DigitCtx& dc,
+                                         uint8_t* dst, int tile_bytes, int cc,
+                                         unsigned long long* s_n2_l) {
+  float n2f = 0.f;
+  if constexpr (BETA > 0) {
+    // plane by plane from the 8 biased fixed-point values: each plane's 16
+    // bytes are stored as soon as they are cut
+    uint32_t lo[8], hi[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) biased_fixed<S, BETA>(x[u], e, dc.bias64, lo[u], hi[u]);
+    uint32_t w0[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float f0 = top_digit<S, BETA>(lo[2 * v], hi[2 * v]);
+      const float f1 = top_digit<S, BETA>(lo[2 * v + 1], hi[2 * v + 1]);
+      w0[v] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+      const float al0 = fabsf(f0) + 0.51f, al1 = fabsf(f1) + 0.51f;
+      n2f = fmaf(al0, al0, n2f);
+      n2f = fmaf(al1, al1, n2f);
+    }
+    *reinterpret_cast<uint4*>(dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+#pragma unroll
+    for (int p = 1; p < S; ++p)
+      *reinterpret_cast<uint4*>(dst + (int64_t)p * tile_bytes) =
+          make_uint4(lower_digit_pair<S, BETA>(p, lo[0], hi[0], lo[1], hi[1]),
+                     lower_digit_pair<S, BETA>(p, lo[2], hi[2], lo[3], hi[3]),
+                     lower_digit_pair<S, BETA>(p, lo[4], hi[4], lo[5], hi[5]),
+                     lower_digit_pair<S, BETA>(p, lo[6], hi[6], lo[7], hi[7]));
+  } else {
+    uint32_t w[S][4];
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      int d0[S], d1[S];
+      const float al0 = make_digits<S>(x[u], e, dc, d0);
+      const float al1 = make_digits<S>(x[u + 1], e, dc, d1);
+#pragma unroll
+      for (int p = 0; p < S; ++p) w[p][u >> 1] = bf16_of_int(d0[p]) | (bf16_of_int(d1[p]) << 16);
+      n2f = fmaf(al0, al0, n2f);
+      n2f = fmaf(al1, al1, n2f);
+    }
+#pragma unroll
+    for (int p = 0; p < S; ++p)
+      *reinterpret_cast<uint4*>(dst + (int64_t)p * tile_bytes) =
+          make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+  }
+  // 8 values of at most 257.51^2 each, in units of 2^-8: < 2^28 per lane; 8 lanes < 2^31
+  uint32_t n2 = __float2uint_ru(n2f * 256.0f * 1.0001f);
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) n2 += __shfl_xor_sync(0xFFFFFFFFu, n2, o);
+  if (cc == 0 && n2) atomicAdd(s_n2_l, (unsigned long long)n2);
+}
+
+// Advances a warp's item (group g of 4 lines, k-block kb) by `step` items in
+// the group-fastest order, without a division.
+__device__ __forceinline__ void next_item(int& g, int& kb, int step, int groups) {
+  g += step;
+  while (g >= groups) {
+    g -= groups;
+    ++kb;
   }
 }
 
@@ -132,6 +250,7 @@ __global__ void __launch_bounds__(kSliceThreads, BETA > 0 ? 5 : 4)
   __shared__ unsigned long long s_max[128];
   __shared__ unsigned long long s_n2[128];  // sum of alpha^2 in units of 2^-8 (rounded up)
   __shared__ int s_e[128];
+  __shared__ LineSrc s_src[128];            // the job's lines, job-relative
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int cc = lane & 7;        // chunk of 8 k values inside a 64-wide k-block
   const int lsub = lane >> 3;     // line within the warp's group of 4
@@ -139,98 +258,57 @@ __global__ void __launch_bounds__(kSliceThreads, BETA > 0 ? 5 : 4)
   for (int64_t jb = blockIdx.x; jb < a.njobs; jb += gridDim.x) {
     const SliceJob J = a.jobs[jb];
     const bool isA = J.side == 0;
+    const bool rows = isA || a.herk;
     const int kv = J.kv;
     const int lines = isA ? BM : a.bn;
     const int groups = J.nl / 4;  // the job's lines [l0, l0 + nl) in groups of 4
-    const int items = groups * J.nkb;
+    if (groups <= 0) continue;    // (the planner makes none; same for every thread)
     const int tile_bytes = lines * kLineBytes;
     uint8_t* tiles = isA ? a.tilesA : a.tilesB;
     if (t < 128) {
       s_max[t] = 0;
       s_n2[t] = 0;
     }
+    if (t < J.nl) s_src[t] = line_src(a, J, isA, J.l0 + t);
     __syncthreads();
-    // ---- phase 1: line maxima (exponents)
-    for (int wi = warp; wi < items; wi += kWarps) {
-      const int l = J.l0 + (wi % groups) * 4 + lsub, kb = wi / groups;
-      const int li = l / J.span;
-      const int line = J.org + l % J.span;
-      SInst in{};
-      bool valid = li < J.g;
-      if (valid) {
-        in = isA ? a.instA[a.orderA[J.pos + li]] : a.instB[a.orderB[J.pos + li]];
-        valid = isA ? line < (a.cplx ? 2 * in.m : in.m) : line < in.n;
+    // ---- phase 1: line maxima (exponents). Lines beyond their instance only
+    // meet discarded outputs: a group of 4 such lines is skipped here and in
+    // phase 2 (its tile rows keep whatever finite digits they hold; the
+    // planner zeroes them once).
+    {
+      int g = 0, kb = 0;
+      next_item(g, kb, warp, groups);
+      while (kb < J.nkb) {
+        const int r = g * 4 + lsub;
+        const LineSrc src = s_src[r];
+        if (__any_sync(0xFFFFFFFFu, src.off >= 0)) {
+          double x[8];
+          load8(a, rows, src, kb * BK + 8 * cc, kv, x);
+          merge_max(x, cc, &s_max[J.l0 + r]);
+        }
+        next_item(g, kb, kWarps, groups);
       }
-      // rows of A / columns of B beyond the instance only meet discarded
-      // outputs: an item of 4 such lines is skipped (its tile rows keep
-      // whatever finite digits they hold; the planner zeroes them once)
-      if (!__any_sync(0xFFFFFFFFu, valid)) continue;
-      double x[8];
-      load8(a, isA, in, valid, line, kb * BK + 8 * cc, kv, x);
-      unsigned long long mx = 0;
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(x[u]) & 0x7FFFFFFFFFFFFFFFull;
-        mx = b > mx ? b : mx;
-      }
-#pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {
-        const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
-        mx = y > mx ? y : mx;
-      }
-      if (cc == 0 && mx) atomicMax(&s_max[l], mx);
     }
     __syncthreads();
     if (t < 128) s_e[t] = line_exponent(s_max[t]);
     __syncthreads();
     // ---- phase 2: digit planes and the norm of the absolute digit weights
-    for (int wi = warp; wi < items; wi += kWarps) {
-      const int l = J.l0 + (wi % groups) * 4 + lsub, kb = wi / groups;
-      const int li = l / J.span;
-      const int line = J.org + l % J.span;
-      SInst in{};
-      bool valid = li < J.g;
-      if (valid) {
-        in = isA ? a.instA[a.orderA[J.pos + li]] : a.instB[a.orderB[J.pos + li]];
-        valid = isA ? line < (a.cplx ? 2 * in.m : in.m) : line < in.n;
-      }
-      if (!__any_sync(0xFFFFFFFFu, valid)) continue;
-      const int e = s_e[l];
-      double x[8];
-      load8(a, isA, in, valid, line, kb * BK + 8 * cc, kv, x);
-      uint32_t w[S][4];
-      float n2f = 0.f;
-#pragma unroll
-      for (int u = 0; u < 8; u += 2) {
-        float al0, al1;
-        if constexpr (BETA > 0) {
-          float f0[S], f1[S];
-          al0 = make_digits_f<S, BETA>(x[u], e, dc.bias64, f0);
-          al1 = make_digits_f<S, BETA>(x[u + 1], e, dc.bias64, f1);
-#pragma unroll
-          for (int p = 0; p < S; ++p)
-            w[p][u >> 1] = __byte_perm(__float_as_uint(f0[p]), __float_as_uint(f1[p]), 0x7632);
-        } else {
-          int d0[S], d1[S];
-          al0 = make_digits<S>(x[u], e, dc, d0);
-          al1 = make_digits<S>(x[u + 1], e, dc, d1);
-#pragma unroll
-          for (int p = 0; p < S; ++p) w[p][u >> 1] = bf16_of_int(d0[p]) | (bf16_of_int(d1[p]) << 16);
+    {
+      int g = 0, kb = 0;
+      next_item(g, kb, warp, groups);
+      while (kb < J.nkb) {
+        const int r = g * 4 + lsub;
+        const LineSrc src = s_src[r];
+        if (__any_sync(0xFFFFFFFFu, src.off >= 0)) {
+          const int l = J.l0 + r;
+          double x[8];
+          load8(a, rows, src, kb * BK + 8 * cc, kv, x);
+          uint8_t* dst = tiles + (J.tile0 + (int64_t)kb * S) * tile_bytes + l * kLineBytes +
+                         ((cc ^ (l & 7)) << 4);
+          cut_item<S, BETA>(x, s_e[l], dc, dst, tile_bytes, cc, &s_n2[l]);
         }
-        n2f = fmaf(al0, al0, n2f);
-        n2f = fmaf(al1, al1, n2f);
+        next_item(g, kb, kWarps, groups);
       }
-      uint8_t* dst = tiles + (J.tile0 + (int64_t)kb * S) * tile_bytes + l * kLineBytes +
-                     ((cc ^ (l & 7)) << 4);
-#pragma unroll
-      for (int p = 0; p < S; ++p)
-        *reinterpret_cast<uint4*>(dst + (int64_t)p * tile_bytes) =
-            make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
-      // 8 values of at most 257.51^2 each, in units of 2^-8: < 2^28 per lane; 8 lanes < 2^31
-      uint32_t n2 = __float2uint_ru(n2f * 256.0f * 1.0001f);
-#pragma unroll
-      for (int o = 1; o < 8; o <<= 1) n2 += __shfl_xor_sync(0xFFFFFFFFu, n2, o);
-      if (cc == 0 && n2) atomicAdd(&s_n2[l], (unsigned long long)n2);
     }
     __syncthreads();
     // ---- phase 3: meta of the job's lines (exponent, norm exponent)

@@ -343,17 +343,12 @@ __device__ __forceinline__ uint32_t bf16_of_int(int d) {
   return __float_as_uint(f) >> 16;
 }
 
-// Digits of round(x 2^(S BETA - e)) with S and BETA known at compile time
-// and S BETA <= 60 (the cut the slice kernels use for the documented modes):
-// the same balanced digits as make_digits, read from the two 32-bit halves
-// of the biased 64-bit fixed-point value with constant shifts, each turned
-// straight into its FP32 value f[p] (exact: |d| <= 256). Returns |d_1| + 0.51,
-// an upper bound of the absolute digit weight sum_p |d_p| 2^(-BETA (p-1))
-// (the lower digits add at most 2^(BETA-1) sum_{j>=1} 2^(-BETA j) < 0.51).
+// round(x 2^(S BETA - e)) + bias as a 64-bit two's-complement value, in its
+// two 32-bit halves (S BETA <= 60: the narrow cut).
 template <int S, int BETA>
-__device__ __forceinline__ float make_digits_f(double x, int e, long long bias, float* f) {
+__device__ __forceinline__ void biased_fixed(double x, int e, long long bias, uint32_t& lo,
+                                             uint32_t& hi) {
   static_assert(S * BETA <= 60, "narrow cut only");
-  constexpr int HALF = 1 << (BETA - 1), MASK = (1 << BETA) - 1;
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int eb = (int)(bits >> 52) & 0x7FF;
   unsigned long long M = bits & ((1ull << 52) - 1);
@@ -371,7 +366,22 @@ __device__ __forceinline__ float make_digits_f(double x, int e, long long bias, 
     else if (sh > -64) N = (M + (1ull << (-sh - 1))) >> (-sh);
   }
   const long long Np = ((bits >> 63) ? -(long long)N : (long long)N) + bias;
-  const uint32_t lo = (uint32_t)Np, hi = (uint32_t)((unsigned long long)Np >> 32);
+  lo = (uint32_t)Np;
+  hi = (uint32_t)((unsigned long long)Np >> 32);
+}
+
+// Digits of round(x 2^(S BETA - e)) with S and BETA known at compile time
+// and S BETA <= 60 (the cut the slice kernels use for the documented modes):
+// the same balanced digits as make_digits, read from the two 32-bit halves
+// of the biased 64-bit fixed-point value with constant shifts, each turned
+// straight into its FP32 value f[p] (exact: |d| <= 256). Returns |d_1| + 0.51,
+// an upper bound of the absolute digit weight sum_p |d_p| 2^(-BETA (p-1))
+// (the lower digits add at most 2^(BETA-1) sum_{j>=1} 2^(-BETA j) < 0.51).
+template <int S, int BETA>
+__device__ __forceinline__ float make_digits_f(double x, int e, long long bias, float* f) {
+  constexpr int HALF = 1 << (BETA - 1), MASK = (1 << BETA) - 1;
+  uint32_t lo, hi;
+  biased_fixed<S, BETA>(x, e, bias, lo, hi);
   // f = float(field - HALF) = as_float(0x4B400000 + field - HALF) - 1.5 * 2^23
   constexpr int kMagic = 0x4B400000 - HALF;
 #pragma unroll
@@ -389,6 +399,57 @@ __device__ __forceinline__ float make_digits_f(double x, int e, long long bias, 
   else top = (int)__funnelshift_r(lo, hi, off0);  // |value| < 2^31 after the shift
   f[0] = __int_as_float(kMagic + top) - 12582912.0f;
   return fabsf(f[0]) + 0.51f;
+}
+
+// a - b on two packed BF16 values (round to nearest; exact for the small
+// integers used here)
+__device__ __forceinline__ uint32_t bf16x2_sub(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("sub.rn.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// Lower digit p >= 1 of make_digits_f for two values at once, from their
+// biased fixed-point halves, packed as the BF16 pair the tiles hold:
+// bf16(d_p(x1)) << 16 | bf16(d_p(x0)). The digit is field - HALF with
+// 0 <= field < 2^BETA <= 128: both fields go under the BF16 pattern of 128
+// (0x4300, whose 7 fraction bits then count units), which makes 128 + field
+// exactly, and one packed BF16 subtraction of 128 + HALF leaves field - HALF,
+// also exact.
+template <int S, int BETA>
+__device__ __forceinline__ uint32_t lower_digit_pair(int p, uint32_t lo0, uint32_t hi0,
+                                                     uint32_t lo1, uint32_t hi1) {
+  static_assert(BETA <= 7, "fields must stay below 128");
+  constexpr int HALF = 1 << (BETA - 1), MASK = (1 << BETA) - 1;
+  constexpr uint32_t kFields = (uint32_t)MASK * 0x10001u;
+  constexpr uint32_t kBase = 0x43004300u;                           // (128, 128)
+  constexpr uint32_t kSub = (0x4300u + (uint32_t)HALF) * 0x10001u;  // (128 + HALF) twice
+  const int off = BETA * (S - 1 - p);
+  uint32_t t0, t1;
+  if (off + BETA <= 32) {
+    t0 = lo0 >> off;
+    t1 = lo1 >> off;
+  } else if (off >= 32) {
+    t0 = hi0 >> (off - 32);
+    t1 = hi1 >> (off - 32);
+  } else {
+    t0 = __funnelshift_r(lo0, hi0, off);
+    t1 = __funnelshift_r(lo1, hi1, off);
+  }
+  return bf16x2_sub((__byte_perm(t0, t1, 0x5410) & kFields) | kBase, kSub);
+}
+
+// Top digit d_1 of make_digits_f (|d_1| <= 2^BETA, possibly below -HALF) as
+// an exact FP32 value, from the biased fixed-point halves.
+template <int S, int BETA>
+__device__ __forceinline__ float top_digit(uint32_t lo, uint32_t hi) {
+  constexpr int HALF = 1 << (BETA - 1);
+  constexpr int kMagic = 0x4B400000 - HALF;
+  constexpr int off0 = BETA * (S - 1);
+  int top;
+  if constexpr (off0 >= 32) top = (int)hi >> (off0 - 32);
+  else top = (int)__funnelshift_r(lo, hi, off0);
+  return __int_as_float(kMagic + top) - 12582912.0f;
 }
 
 // Norm exponent: smallest R with sqrt(S) < 2^R (with a margin for the FP32

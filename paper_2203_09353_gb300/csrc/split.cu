@@ -124,8 +124,13 @@ __device__ __forceinline__ void load8(const SliceArgs& a, bool rows, LineSrc src
   if (rows) {
     if (!a.cplx) {
       const double* p = a.A + src.off + (int64_t)q0 * ld;
+      if (q0 + 8 <= kv) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) x[u] = q0 + u < kv ? __ldg(p + (int64_t)u * ld) : 0.0;
+        for (int u = 0; u < 8; ++u) x[u] = __ldg(p + (int64_t)u * ld);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = q0 + u < kv ? __ldg(p + (int64_t)u * ld) : 0.0;
+      }
     } else {
       const double2* p = reinterpret_cast<const double2*>(a.A) + src.off + (int64_t)(q0 >> 1) * ld;
       const bool im_row = src.ldx & 1;
@@ -141,6 +146,15 @@ __device__ __forceinline__ void load8(const SliceArgs& a, bool rows, LineSrc src
     // 16-byte loads where the column allows them (a real B with an odd ldb or
     // offset puts every other column on an 8-byte boundary)
     const bool vec = (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+    if (vec && q0 + 8 <= kv) {
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        const double2 z = __ldg(reinterpret_cast<const double2*>(p + u));
+        x[u] = z.x;
+        x[u + 1] = z.y;
+      }
+      return;
+    }
 #pragma unroll
     for (int u = 0; u < 8; u += 2) {
       if (vec && q0 + u + 1 < kv) {
@@ -156,19 +170,25 @@ __device__ __forceinline__ void load8(const SliceArgs& a, bool rows, LineSrc src
 }
 
 // Line maximum of the 8 values of a lane, merged over the 8 lanes of the line
-// and into s_max.
+// and into s_max. Only line_exponent of the largest |x| is used, and it sees
+// the same value in the pair of separate maxima of the 32-bit halves (sign
+// cleared): the exponent field sits in the high half, and where every
+// exponent is zero, the largest high half, or when those are all zero the
+// largest low half, holds the highest fraction bit. Merging such pairs as
+// 64-bit values keeps this.
 __device__ __forceinline__ void merge_max(const double (&x)[8], int cc, unsigned long long* s_max_l) {
-  unsigned long long mx = 0;
+  uint32_t mh = 0, ml = 0;
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x[u]) & 0x7FFFFFFFFFFFFFFFull;
-    mx = b > mx ? b : mx;
+    mh = max(mh, (uint32_t)__double2hiint(x[u]) & 0x7FFFFFFFu);
+    ml = max(ml, (uint32_t)__double2loint(x[u]));
   }
 #pragma unroll
   for (int o = 1; o < 8; o <<= 1) {
-    const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
-    mx = y > mx ? y : mx;
+    mh = max(mh, __shfl_xor_sync(0xFFFFFFFFu, mh, o));
+    ml = max(ml, __shfl_xor_sync(0xFFFFFFFFu, ml, o));
   }
+  const unsigned long long mx = (unsigned long long)mh << 32 | ml;
   if (cc == 0 && mx) atomicMax(s_max_l, mx);
 }
 

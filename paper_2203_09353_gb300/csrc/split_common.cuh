@@ -370,37 +370,6 @@ __device__ __forceinline__ void biased_fixed(double x, int e, long long bias, ui
   hi = (uint32_t)((unsigned long long)Np >> 32);
 }
 
-// Digits of round(x 2^(S BETA - e)) with S and BETA known at compile time
-// and S BETA <= 60 (the cut the slice kernels use for the documented modes):
-// the same balanced digits as make_digits, read from the two 32-bit halves
-// of the biased 64-bit fixed-point value with constant shifts, each turned
-// straight into its FP32 value f[p] (exact: |d| <= 256). Returns |d_1| + 0.51,
-// an upper bound of the absolute digit weight sum_p |d_p| 2^(-BETA (p-1))
-// (the lower digits add at most 2^(BETA-1) sum_{j>=1} 2^(-BETA j) < 0.51).
-template <int S, int BETA>
-__device__ __forceinline__ float make_digits_f(double x, int e, long long bias, float* f) {
-  constexpr int HALF = 1 << (BETA - 1), MASK = (1 << BETA) - 1;
-  uint32_t lo, hi;
-  biased_fixed<S, BETA>(x, e, bias, lo, hi);
-  // f = float(field - HALF) = as_float(0x4B400000 + field - HALF) - 1.5 * 2^23
-  constexpr int kMagic = 0x4B400000 - HALF;
-#pragma unroll
-  for (int p = S - 1; p >= 1; --p) {
-    const int off = BETA * (S - 1 - p);
-    uint32_t field;
-    if (off + BETA <= 32) field = (lo >> off) & MASK;
-    else if (off >= 32) field = (hi >> (off - 32)) & MASK;
-    else field = __funnelshift_r(lo, hi, off) & MASK;
-    f[p] = __int_as_float(kMagic + (int)field) - 12582912.0f;
-  }
-  constexpr int off0 = BETA * (S - 1);
-  int top;
-  if constexpr (off0 >= 32) top = (int)hi >> (off0 - 32);
-  else top = (int)__funnelshift_r(lo, hi, off0);  // |value| < 2^31 after the shift
-  f[0] = __int_as_float(kMagic + top) - 12582912.0f;
-  return fabsf(f[0]) + 0.51f;
-}
-
 // a - b on two packed BF16 values (round to nearest; exact for the small
 // integers used here)
 __device__ __forceinline__ uint32_t bf16x2_sub(uint32_t a, uint32_t b) {
@@ -409,13 +378,19 @@ __device__ __forceinline__ uint32_t bf16x2_sub(uint32_t a, uint32_t b) {
   return d;
 }
 
-// Lower digit p >= 1 of make_digits_f for two values at once, from their
-// biased fixed-point halves, packed as the BF16 pair the tiles hold:
-// bf16(d_p(x1)) << 16 | bf16(d_p(x0)). The digit is field - HALF with
-// 0 <= field < 2^BETA <= 128: both fields go under the BF16 pattern of 128
-// (0x4300, whose 7 fraction bits then count units), which makes 128 + field
-// exactly, and one packed BF16 subtraction of 128 + HALF leaves field - HALF,
-// also exact.
+// The balanced digits of make_digits with S and BETA known at compile time
+// and S BETA <= 60 (the cut the slice kernels use for the documented modes),
+// read from the two 32-bit halves of the biased 64-bit fixed-point value
+// (biased_fixed) with constant shifts: digit p (1-based) is the BETA-bit field
+// at bit BETA (S - p), minus HALF, the top one the arithmetic remainder above.
+//
+// Lower digit p >= 2 (index p - 1 >= 1) for two values at once, packed as the
+// BF16 pair the tiles hold: bf16(d(x1)) << 16 | bf16(d(x0)). The digit is
+// field - HALF with 0 <= field < 2^BETA <= 128: both fields go under the BF16
+// pattern of 128 (0x4300, whose 7 fraction bits then count units), which makes
+// 128 + field exactly, and one packed BF16 subtraction of 128 + HALF leaves
+// field - HALF, also exact. A field inside one 16-bit window of a 32-bit half
+// is gathered for both values with one byte permute and one shift.
 template <int S, int BETA>
 __device__ __forceinline__ uint32_t lower_digit_pair(int p, uint32_t lo0, uint32_t hi0,
                                                      uint32_t lo1, uint32_t hi1) {
@@ -425,21 +400,26 @@ __device__ __forceinline__ uint32_t lower_digit_pair(int p, uint32_t lo0, uint32
   constexpr uint32_t kBase = 0x43004300u;                           // (128, 128)
   constexpr uint32_t kSub = (0x4300u + (uint32_t)HALF) * 0x10001u;  // (128 + HALF) twice
   const int off = BETA * (S - 1 - p);
-  uint32_t t0, t1;
-  if (off + BETA <= 32) {
-    t0 = lo0 >> off;
-    t1 = lo1 >> off;
-  } else if (off >= 32) {
-    t0 = hi0 >> (off - 32);
-    t1 = hi1 >> (off - 32);
+  uint32_t both;
+  if (off + BETA <= 32 || off >= 32) {
+    const uint32_t w0 = off >= 32 ? hi0 : lo0, w1 = off >= 32 ? hi1 : lo1;
+    const int o = off >= 32 ? off - 32 : off;  // field at bits [o, o + BETA) of w
+    const int b = o / 8 < 2 ? o / 8 : 2;       // 16-bit window from byte b
+    if (o - 8 * b + BETA <= 16) {
+      // bytes b, b+1 of w0 below bytes b, b+1 of w1, then one shift for both
+      const uint32_t sel = (uint32_t)b | (uint32_t)(b + 1) << 4 | (uint32_t)(b + 4) << 8 |
+                           (uint32_t)(b + 5) << 12;
+      both = __byte_perm(w0, w1, sel) >> (o - 8 * b);
+    } else {
+      both = __byte_perm(w0 >> o, w1 >> o, 0x5410);
+    }
   } else {
-    t0 = __funnelshift_r(lo0, hi0, off);
-    t1 = __funnelshift_r(lo1, hi1, off);
+    both = __byte_perm(__funnelshift_r(lo0, hi0, off), __funnelshift_r(lo1, hi1, off), 0x5410);
   }
-  return bf16x2_sub((__byte_perm(t0, t1, 0x5410) & kFields) | kBase, kSub);
+  return bf16x2_sub((both & kFields) | kBase, kSub);
 }
 
-// Top digit d_1 of make_digits_f (|d_1| <= 2^BETA, possibly below -HALF) as
+// Top digit d_1 (|d_1| <= 2^BETA, possibly below -HALF) as
 // an exact FP32 value, from the biased fixed-point halves.
 template <int S, int BETA>
 __device__ __forceinline__ float top_digit(uint32_t lo, uint32_t hi) {

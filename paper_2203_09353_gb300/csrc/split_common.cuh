@@ -344,28 +344,28 @@ __device__ __forceinline__ uint32_t bf16_of_int(int d) {
 }
 
 // round(x 2^(S BETA - e)) + bias as a 64-bit two's-complement value, in its
-// two 32-bit halves (S BETA <= 60: the narrow cut).
+// two 32-bit halves (S BETA <= 60: the narrow cut); ties round away from zero.
+// With |x| = M 2^(q) (M < 2^53 the integer significand), the magnitude is
+// M >> r rounded, r = e - S BETA - q: (M + 2^(r-1)) >> r, computed as
+// ((M >> (r-1)) + 1) >> 1, and 0 once r > 53. A non-positive r (a line of
+// subnormals only) shifts left.
 template <int S, int BETA>
 __device__ __forceinline__ void biased_fixed(double x, int e, long long bias, uint32_t& lo,
                                              uint32_t& hi) {
   static_assert(S * BETA <= 60, "narrow cut only");
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const int eb = (int)(bits >> 52) & 0x7FF;
-  unsigned long long M = bits & ((1ull << 52) - 1);
-  int q;
-  if (eb == 0) {
-    q = -1074;
+  const uint32_t xh = (uint32_t)__double2hiint(x), xl = (uint32_t)__double2loint(x);
+  const int eb = (int)(xh >> 20) & 0x7FF;
+  const unsigned long long M =
+      (unsigned long long)((xh & 0xFFFFFu) | (eb != 0 ? 0x100000u : 0u)) << 32 | xl;
+  // q = max(eb, 1) - 1075
+  const int r = e - S * BETA + 1075 - (eb > 1 ? eb : 1);
+  unsigned long long N;
+  if (r >= 1) {
+    N = r <= 53 ? ((M >> (r - 1)) + 1) >> 1 : 0ull;
   } else {
-    M |= 1ull << 52;
-    q = eb - 1075;
+    N = M << (-r);
   }
-  const int sh = q - e + S * BETA;
-  unsigned long long N = 0;
-  if (M != 0) {
-    if (sh >= 0) N = M << sh;
-    else if (sh > -64) N = (M + (1ull << (-sh - 1))) >> (-sh);
-  }
-  const long long Np = ((bits >> 63) ? -(long long)N : (long long)N) + bias;
+  const long long Np = ((xh >> 31) ? -(long long)N : (long long)N) + bias;
   lo = (uint32_t)Np;
   hi = (uint32_t)((unsigned long long)Np >> 32);
 }

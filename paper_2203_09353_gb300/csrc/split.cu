@@ -259,12 +259,13 @@ __device__ __forceinline__ void next_item(int& g, int& kb, int step, int groups)
 }
 
 // BETA > 0: compile-time digit width (S * BETA <= 60); BETA == 0: any width a.beta.
-// The compile-time cuts run five CTAs per SM (at most 51 registers a thread):
-// the kernel is bound by memory latency, and 40 warps per SM hide it better
-// than 32 (measured 4.6 -> 4.4 ms for 9 slices on the 20000-instance size
-// mix). The generic cut keeps four, where five would spill.
+// The compile-time cuts run six CTAs per SM (at most 40 registers a thread):
+// the kernel is bound by memory latency, and 48 warps per SM hide it better
+// than 40 (measured 3.41 -> 3.35 ms for 9 slices on the 20000-instance size
+// mix; seven or eight CTAs spill and are slower). The generic cut keeps four,
+// where five would spill.
 template <int S, int BETA>
-__global__ void __launch_bounds__(kSliceThreads, BETA > 0 ? 5 : 4)
+__global__ void __launch_bounds__(kSliceThreads, BETA > 0 ? 6 : 4)
     split_slice_kernel(const SliceArgs a) {
   const DigitCtx dc = digit_ctx<S>(BETA > 0 ? BETA : a.beta);
   __shared__ unsigned long long s_max[128];

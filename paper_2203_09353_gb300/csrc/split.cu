@@ -262,7 +262,7 @@ __device__ __forceinline__ void next_item(int& g, int& kb, int step, int groups)
 // The compile-time cuts run six CTAs per SM (at most 40 registers a thread):
 // the kernel is bound by memory latency, and 48 warps per SM hide it better
 // than 40 (measured 3.41 -> 3.35 ms for 9 slices on the 20000-instance size
-// mix; seven or eight CTAs spill and are slower). The generic cut keeps four,
+// mix; seven or eight CTAs, with fewer registers, are slower). The generic cut keeps four,
 // where five would spill.
 template <int S, int BETA>
 __global__ void __launch_bounds__(kSliceThreads, BETA > 0 ? 6 : 4)

@@ -44,10 +44,10 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # divided by that batch's algorithmic bytes (990601216): a full launch's traffic
 # is this ratio times its own algorithmic bytes. Valid only while the split kernel sources
 # hash to NCU_SOURCES_SHA; otherwise the traffic is reported as null.
-NCU_TRAFFIC_PER_BYTE = {"split9": {"gemm": 1.806461e9 / 990601216.0,
-                                   "slicer": 1.739163e9 / 990601216.0}}
+NCU_TRAFFIC_PER_BYTE = {"split9": {"gemm": 1.806581e9 / 990601216.0,
+                                   "slicer": 1.810911e9 / 990601216.0}}
 NCU_SOURCES = ("split.cu", "split_common.cuh", "split_gemm.cuh", "split_gemm_r64.cu")
-NCU_SOURCES_SHA = "8a09d544aa82a291"
+NCU_SOURCES_SHA = "26b002273f289b6f"
 
 
 def split_sources_sha() -> str:

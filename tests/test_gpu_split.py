@@ -245,3 +245,51 @@ def test_long_k_multipass_sampled_rows(gpu, s):
             # normwise for the row: ||c_r - ref_r|| / (||a_r|| ||B||)
             den = np.linalg.norm(a[r::m][:k]) * np.linalg.norm(b)
             assert np.linalg.norm(row_got - row_ref) / den <= TOL_SPLIT.get(s, 1e-6), (s, i, r)
+
+
+@pytest.mark.parametrize("s", [3, 6, 9])
+@pytest.mark.parametrize("dtype", ["r64", "c128"])
+def test_split_extreme_exponents(gpu, dtype, s):
+    """Operands at both ends of the FP64 range: A (or B) made of subnormal
+    values only, which takes the fixed-point cut's left shift and the line
+    maximum of a subnormal line; near-overflow operands; rows that are zero or
+    subnormal next to normal ones. The product is representable in every case.
+    The error is measured in exactly rescaled norms (powers of two), since the
+    plain norms of subnormal operands underflow."""
+    rng = np.random.default_rng(21)
+    # (m, n, k) and the binary scale of A and of B
+    cases = [((24, 20, 40), -1060, 1000), ((17, 33, 70), -1072, 1010),
+             ((24, 20, 40), 900, 100), ((20, 24, 40), 1000, -1050), ((40, 40, 40), 0, 0)]
+    table, la, lb, lc = synth.pack_table([c[0] for c in cases])
+    cplx = dtype == "c128"
+    dt = np.complex128 if cplx else np.float64
+    A, B, C = np.zeros(la, dt), np.zeros(lb, dt), np.zeros(lc, dt)
+
+    def fill(shape, scale):
+        x = rng.uniform(-1, 1, shape)
+        if cplx:
+            x = x + 1j * rng.uniform(-1, 1, shape)
+        return x * 2.0 ** scale if abs(scale) < 1000 else x * 2.0 ** (scale // 2) * 2.0 ** (scale - scale // 2)
+
+    for i, ((m, n, k), sa, sb) in enumerate(cases):
+        _, _, _, lda, ldb, ldc, ao, bo, co = (int(v) for v in table[i])
+        a, b = fill((m, k), sa), fill((k, n), sb)
+        if i == 4:
+            a[3, :] = 0.0                       # a zero row
+            a[5, :] = fill(k, -1074 + 8)        # a row of tiny subnormals among normal ones
+            a[7, 2] = 5e-324                    # the smallest subnormal in a normal row
+        A[ao:ao + lda * k] = np.asfortranarray(a).ravel(order="F")
+        B[bo:bo + ldb * n] = np.asfortranarray(b).ravel(order="F")
+    batch = synth.Batch("extreme", dtype, table, A, B, C, 1.0, 0.0)
+    ref = oracle_batch(batch)
+    got, _ = run_grouped(batch, split(s))
+    got = host(got)
+    for i, ((m, n, k), sa, sb) in enumerate(cases):
+        _, _, _, lda, ldb, ldc, ao, bo, co = (int(v) for v in table[i])
+        g = got[co:co + ldc * n].reshape(n, ldc).T[:m, :]
+        r = ref[co:co + ldc * n].reshape(n, ldc).T[:m, :]
+        assert np.all(np.isfinite(g)), i
+        num = np.linalg.norm(np.ldexp(np.abs(g - r), -(sa + sb)))
+        a = np.ldexp(np.abs(batch.instance(i, "A")), -sa)
+        b = np.ldexp(np.abs(batch.instance(i, "B")), -sb)
+        assert num <= TOL_SPLIT[s] * np.linalg.norm(a) * np.linalg.norm(b), (i, num)

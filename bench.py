@@ -47,7 +47,7 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 NCU_TRAFFIC_PER_BYTE = {"split9": {"gemm": 1.806581e9 / 990601216.0,
                                    "slicer": 1.810911e9 / 990601216.0}}
 NCU_SOURCES = ("split.cu", "split_common.cuh", "split_gemm.cuh", "split_gemm_r64.cu")
-NCU_SOURCES_SHA = "26b002273f289b6f"
+NCU_SOURCES_SHA = "1093ee09442d5f89"
 
 
 def split_sources_sha() -> str:

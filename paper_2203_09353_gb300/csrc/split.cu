@@ -33,10 +33,11 @@
 //
 // Kernels:
 //  * split_slice_kernel: one CTA per line block (128 rows of A, or BN columns
-//    of B): exponents, digit planes written as pre-swizzled BF16 tiles of 64 k
-//    (the exact SWIZZLE_128B K-major shared-memory image), the s planes of one
-//    k-block stored next to each other, per-line norm exponents. Integer
-//    arithmetic only.
+//    of B), or per part of one: exponents, digit planes written as
+//    pre-swizzled BF16 tiles of 64 k (the exact SWIZZLE_128B K-major
+//    shared-memory image), the s planes of one k-block stored next to each
+//    other, per-line norm exponents. Integer arithmetic, plus exact
+//    conversions of small integers to FP32 and BF16.
 //  * split_gemm_kernel<BN>: persistent, one CTA per SM, warp-specialised.
 //    Output tile 128 x BN with BN = the largest multiple of 16 with
 //    s BN <= 512, so that the s level accumulators (one per t) all live in

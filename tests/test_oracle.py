@@ -327,3 +327,26 @@ def test_synth_config_shapes():
                        pool_small=4, pool_large=2)
     assert ch.idx.shape == (5, 4)
     assert ch.idx[:, :3].max() < 4 and ch.idx[:, 3].max() < 2
+
+
+def test_chain_layout_round_trip():
+    """The packed chain (pool, states, global index table) gives back every
+    pool entry, start state and per-step operator it was built from."""
+    ch = synth.annealing_chain(walkers_small=3, walkers_large=2, n_small=8, n_large=16, steps=4,
+                               pool_small=5, pool_large=3)
+    pool, pool_n, pool_off, states, state_off, gidx = synth.chain_layout(ch)
+    assert gidx.shape == ch.idx.shape and gidx.dtype == np.int32
+    assert pool.size == int(np.sum(pool_n * pool_n)) and states.size == int(np.sum(ch.n_walker ** 2))
+
+    def entry(j):
+        n = int(pool_n[j])
+        return pool[pool_off[j]:pool_off[j] + n * n].reshape(n, n).T
+
+    for w in range(ch.walkers):
+        n = int(ch.n_walker[w])
+        got = states[state_off[w]:state_off[w] + n * n].reshape(n, n).T
+        assert np.array_equal(got, ch.C0[w])
+        for t in range(ch.steps):
+            j = int(gidx[t, w])
+            assert pool_n[j] == n
+            assert np.array_equal(entry(j), ch.pools[n][ch.idx[t, w]])

@@ -41,8 +41,8 @@ import numpy as np
 
 ALIGN_ELEMS = 32  # 256 B for FP64, 512 B for complex128
 
-CONFIG3_SIZES = (16, 32, 64, 128, 256, 512)
-CONFIG3_WEIGHTS = (0.30, 0.25, 0.20, 0.15, 0.07, 0.03)
+SIZE_MIX_SIZES = (16, 32, 64, 128, 256, 512)
+SIZE_MIX_WEIGHTS = (0.30, 0.25, 0.20, 0.15, 0.07, 0.03)
 
 
 @dataclass
@@ -205,7 +205,7 @@ def hermitian_unitary_c128(batch: int = 4096, n: int = 64) -> Batch:
                  meta={"fixed": (n, n, n, batch)})
 
 
-def draw_sizes(rng, count: int, sizes=CONFIG3_SIZES, weights=CONFIG3_WEIGHTS) -> np.ndarray:
+def draw_sizes(rng, count: int, sizes=SIZE_MIX_SIZES, weights=SIZE_MIX_WEIGHTS) -> np.ndarray:
     return rng.choice(np.asarray(sizes, dtype=np.int64), size=count, p=np.asarray(weights))
 
 
@@ -222,8 +222,8 @@ def _gap_mask(table: np.ndarray, length: int, rows: int, cols: int, ld: int, off
     return keep
 
 
-def mixed_batch(seed: int, count: int, values: str, alpha=1.0, beta=0.5, sizes=CONFIG3_SIZES,
-                weights=CONFIG3_WEIGHTS, name: str | None = None) -> Batch:
+def mixed_batch(seed: int, count: int, values: str, alpha=1.0, beta=0.5, sizes=SIZE_MIX_SIZES,
+                weights=SIZE_MIX_WEIGHTS, name: str | None = None) -> Batch:
     """Grouped real batch of square instances with sizes drawn from ``sizes``.
 
     ``values`` is "uniform" (U[-1, 1]) or "loguniform" (10^U(-4,4), random sign).

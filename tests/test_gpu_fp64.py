@@ -104,11 +104,12 @@ def test_empty_batch_is_noop(gpu):
     assert np.array_equal(host(Cd), b.C)
 
 
-@pytest.mark.parametrize("config", [3, 4])
-def test_grouped_mixed_sizes_reduced(gpu, config):
-    """Configs 3/4 size mix (all six classes present) at a reduced count, one persistent launch."""
-    b = synth.size_mix_uniform(count=160) if config == 3 else synth.size_mix_loguniform(count=160)
-    assert set(np.unique(b.table[:, 0])) == set(synth.CONFIG3_SIZES)
+@pytest.mark.parametrize("values", ["uniform", "loguniform"])
+def test_grouped_mixed_sizes_reduced(gpu, values):
+    """The size mix (all six classes present), U[-1, 1] and log-uniform values, at a
+    reduced count, one persistent launch."""
+    b = synth.size_mix_uniform(count=160) if values == "uniform" else synth.size_mix_loguniform(count=160)
+    assert set(np.unique(b.table[:, 0])) == set(synth.SIZE_MIX_SIZES)
     C, plan = run_grouped(b)
     assert plan.info()["launches_per_call"] == 1
     e = errors(b, host(C), oracle_batch(b))

@@ -317,7 +317,7 @@ def test_synth_config_shapes():
         assert np.linalg.norm(np.conj(U.T) @ U - np.eye(64)) < 1e-13
     b3 = synth.size_mix_uniform(count=300)
     ns = b3.table[:, 0]
-    assert set(np.unique(ns)).issubset(set(synth.CONFIG3_SIZES))
+    assert set(np.unique(ns)).issubset(set(synth.SIZE_MIX_SIZES))
     assert np.all(b3.table[:, 6] % synth.ALIGN_ELEMS == 0)
     b4 = synth.size_mix_loguniform(count=50)
     mags = np.abs(b4.A[b4.A != 0])

@@ -1,7 +1,9 @@
 """CPU oracle for the batched GEMM of Eq. (1) (Sec. 2) -- TEST INFRASTRUCTURE ONLY.
 
 C_i = alpha * A_i * B_i + beta * C_i over N independent instances, in FP64
-and complex128, written out as a plain triple loop in C (``oracle_gemm.c``).
+and complex128, written out as a plain triple loop in C (``oracle_gemm.c``);
+and the local two-spin gate of the annealing step (Sec. 2, "Apply Local
+Gate") on a batch of state vectors (``oracle_gate.c``).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package. The GPU library never calls it and the
@@ -30,6 +32,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle_gemm.c")
+_SRCS = (_SRC, os.path.join(_HERE, "oracle_gate.c"))
 _LIB_NAME = "liboracle.so"
 _lock = threading.Lock()
 _libs: dict[str, ctypes.CDLL] = {}
@@ -46,8 +49,9 @@ def build(out_dir: str | None = None, mutant: int = 0, force: bool = False) -> s
     out_dir = out_dir or _HERE
     name = _LIB_NAME if mutant == 0 else f"liboracle_mutant{mutant}.so"
     path = os.path.join(out_dir, name)
-    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
-        cmd = ["gcc", *_CFLAGS, f"-DORACLE_MUTANT={int(mutant)}", _SRC, "-o", path + ".tmp"]
+    if force or not os.path.exists(path) or \
+            os.path.getmtime(path) < max(os.path.getmtime(f) for f in _SRCS):
+        cmd = ["gcc", *_CFLAGS, f"-DORACLE_MUTANT={int(mutant)}", *_SRCS, "-o", path + ".tmp"]
         subprocess.run(cmd, check=True)
         os.replace(path + ".tmp", path)
     return path
@@ -64,6 +68,8 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     for f in ("oracle_gemm_r64", "oracle_gemm_c128", "oracle_gemm_grouped_r64",
               "oracle_gemm_grouped_c128"):
         getattr(lib, f).restype = None
+    lib.oracle_two_site_gate_c128.argtypes = [i64, ctypes.c_int32, vp, vp, vp, i64]
+    lib.oracle_two_site_gate_c128.restype = i64
     lib.oracle_max_threads.restype = ctypes.c_int
     lib.oracle_set_threads.argtypes = [ctypes.c_int]
     return lib
@@ -155,3 +161,26 @@ def unitarity_drift(C: np.ndarray, lib: ctypes.CDLL | None = None) -> float:
     n = C.shape[0]
     G = matmul(np.conj(C.T), C, lib=lib)
     return float(np.sqrt(np.sum(np.abs(G - np.eye(n)) ** 2)))
+
+
+def two_site_gate(states: np.ndarray, S: int, sites, gates: np.ndarray,
+                  lib: ctypes.CDLL | None = None) -> np.ndarray:
+    """The local two-spin gate on a batch of state vectors; returns the new states.
+
+    ``states``: complex128 [walkers, 2^S] (walker w's amplitude of basis state
+    x, spin i being bit i of x). ``sites``: the lower spin j of each walker's
+    pair (0 <= j <= S - 2). ``gates``: complex128 [walkers, 4, 4], gate[w][a, c]
+    acting on the local index a = b_j + 2 b_{j+1}. Raises ValueError for a bad site.
+    """
+    lib = lib or load()
+    st = np.ascontiguousarray(states, dtype=np.complex128).copy()
+    W = st.shape[0]
+    assert st.shape == (W, 1 << S)
+    sites = np.ascontiguousarray(sites, dtype=np.int32)
+    assert sites.shape == (W,)
+    g = np.ascontiguousarray(np.asarray(gates, dtype=np.complex128).transpose(0, 2, 1))
+    assert g.shape == (W, 4, 4)  # column-major 4 x 4 per walker
+    bad = lib.oracle_two_site_gate_c128(W, int(S), _ptr(sites), _ptr(g), _ptr(st), 1 << S)
+    if bad:
+        raise ValueError(f"{bad} walker(s) with a site outside 0..S-2")
+    return st

@@ -226,6 +226,24 @@ bg_status chain_step(const bg_plan* plan, const void* U_pool, const int32_t* U_i
 
 void bg_plan_destroy(bg_plan* plan);
 
+/* ---- local two-spin gate (Alg. 1, "Apply Local Gate") ----------------------
+ * Sec. 2: every Monte Carlo step first applies a unitary to a neighbouring
+ * pair of spins of the state. For W state vectors of 2^spins amplitudes, in
+ * place:
+ *   psi_w'[x] = sum_{c=0..3} U_w[a(x), c] * psi_w[x - a(x) 2^j + c 2^j],
+ *   a(x) = b_j(x) + 2 b_{j+1}(x),
+ * where b_i(x) is bit i of the basis index x (spin i) and j = sites[w].
+ * dtype: BG_C128 only (BG_ERR_UNSUPPORTED otherwise); 2 <= spins <= 40.
+ * states: DEVICE, walker w's amplitudes at states + w * stride complex
+ *   elements (stride >= 2^spins), interleaved (re, im), 16-byte aligned.
+ * sites: DEVICE int32 [walkers], 0 <= sites[w] <= spins - 2. A walker whose
+ *   site lies outside that range is left unchanged, and the device error word
+ *   records BG_ERR_INVALID_ARG (read it with bg_check_device_errors).
+ * gates: DEVICE, 16 complex per walker, U_w column-major (U[a, c] at a + 4 c).
+ * Caller-owned memory, nothing allocated; asynchronous on `stream`. */
+bg_status apply_local_gate(bg_dtype dtype, int64_t walkers, int32_t spins, const int32_t* sites,
+                           const void* gates, void* states, int64_t stride, bg_stream_t stream);
+
 /* Plan introspection: number of instances, of device work items per grouped
  * call, of kernel launches per grouped call (or per chain step), workspace
  * bytes, and the size classes. */

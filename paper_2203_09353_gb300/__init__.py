@@ -39,7 +39,7 @@ EXPORTS = ("batched_gemm_fixed", "batched_gemm_fixed_static", "batched_gemm_plan
            "bg_plan_kernel_times", "bg_rel_err",
            "bg_unitarity_drift", "bg_split_planes", "bg_check_device_errors",
            "bg_test_bounded_wait", "bg_probe_fp64_peak", "bg_launch_count", "bg_status_string",
-           "bg_last_error", "bg_version")
+           "bg_last_error", "bg_version", "apply_local_gate")
 
 
 class BgemmError(RuntimeError):
@@ -95,6 +95,7 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "bg_check_device_errors": [vp],
         "bg_test_bounded_wait": [i64, vp],
         "bg_probe_fp64_peak": [i32, P(dbl), vp],
+        "apply_local_gate": [i32, i64, i32, vp, vp, vp, i64, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -314,6 +315,24 @@ def unitarity_drift(dtype, d_n, d_off, C, out, count: int, stream=None) -> None:
     """||C_w^H C_w - I||_F per square matrix into the device tensor ``out``."""
     _check(load_library().bg_unitarity_drift(dtype_code(dtype), count, _ptr(d_n), _ptr(d_off),
                                              _ptr(C), _ptr(out), _stream(stream)))
+
+
+def apply_local_gate(states, spins: int, sites, gates, walkers: int | None = None,
+                     stride: int | None = None, stream=None) -> None:
+    """The local two-spin gate (Alg. 1, "Apply Local Gate") on device state vectors, in place.
+
+    ``states``: complex128 device tensor, walker w's 2^spins amplitudes at
+    element w * stride (default stride 2^spins); ``sites``: int32 device tensor
+    [walkers], the lower spin j of each pair; ``gates``: complex128 device
+    tensor of 16 entries per walker, U_w column-major (U[a, c] at a + 4 c) for
+    the local index a = b_j + 2 b_{j+1}. A bad site is reported through the
+    device error word (check_device_errors)."""
+    stride = (1 << spins) if stride is None else int(stride)
+    if walkers is None:
+        walkers = int(sites.numel())
+    _check(load_library().apply_local_gate(dtype_code("c128"), int(walkers), int(spins),
+                                           _ptr(sites), _ptr(gates), _ptr(states), stride,
+                                           _stream(stream)))
 
 
 def split_planes(m, k, X, ldx, axis, slices, beta_bits, exps, digits, stream=None) -> None:

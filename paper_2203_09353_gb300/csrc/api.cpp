@@ -1120,6 +1120,28 @@ bg_status bg_unitarity_drift(bg_dtype dtype, int64_t count, const int64_t* d_n,
   return BG_OK;
 }
 
+bg_status apply_local_gate(bg_dtype dtype, int64_t walkers, int32_t spins, const int32_t* sites,
+                           const void* gates, void* states, int64_t stride, bg_stream_t stream) {
+  bg_status s = check_dtype(dtype);
+  if (s != BG_OK) return s;
+  if (dtype != BG_C128) return fail(BG_ERR_UNSUPPORTED, "the local gate acts on complex128 states");
+  if (walkers < 0) return fail(BG_ERR_INVALID_ARG, "negative walker count");
+  if (spins < 2 || spins > 40) return fail(BG_ERR_INVALID_ARG, "spins must be 2..40");
+  if (stride < ((int64_t)1 << spins))
+    return fail(BG_ERR_INVALID_ARG, "stride below 2^spins amplitudes");
+  if (walkers == 0) return BG_OK;
+  if (!sites || !gates || !states) return fail(BG_ERR_INVALID_ARG, "null pointer");
+  if (!aligned(gates, BG_C128) || !aligned(states, BG_C128))
+    return fail(BG_ERR_INVALID_ARG, "gates or states not 16-byte aligned");
+  DeviceCtx* ctx;
+  s = get_ctx(&ctx);
+  if (s != BG_OK) return s;
+  cudaError_t e = launch_local_gate(walkers, spins, sites, gates, states, stride, ctx->d_err,
+                                    ctx->sms, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "local gate launch");
+  return BG_OK;
+}
+
 bg_status bg_split_planes(int64_t m, int64_t k, const double* X, int64_t ldx, int32_t axis,
                           int32_t slices, int32_t beta_bits, int32_t* exps, uint16_t* digits,
                           bg_stream_t stream) {

@@ -89,6 +89,9 @@ cudaError_t launch_drift(bg_dtype dt, int64_t count, const int64_t* d_n, const i
                          const void* C, double* out, cudaStream_t st);
 cudaError_t launch_bounded_wait(int64_t spin_limit, int* d_err, cudaStream_t st);
 cudaError_t run_fp64_peak_probe(int mma_kind, int sms, double* tflops, cudaStream_t st);
+// Local two-spin gate on a batch of complex128 state vectors (gate.cu).
+cudaError_t launch_local_gate(int64_t walkers, int spins, const int32_t* sites, const void* gates,
+                              void* states, int64_t stride, int* d_err, int sms, cudaStream_t st);
 
 // Device error word layout: [0] = first error code, [1] = location id,
 // [2] = detail, [3] = count of events.
@@ -100,7 +103,8 @@ enum DevErrLoc : int {
   ERRLOC_SPLIT_ACC_FULL = 4,
   ERRLOC_SPLIT_ACC_EMPTY = 5,
   ERRLOC_SPLIT_TMEM_ALLOC = 6,
-  ERRLOC_CHAIN_INDEX = 7
+  ERRLOC_CHAIN_INDEX = 7,
+  ERRLOC_GATE_SITE = 8
 };
 
 // Host bookkeeping.

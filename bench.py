@@ -75,6 +75,8 @@ def parse_args():
     p.add_argument("--e2e-chunks", type=int, default=4, help="instance ranges of the e2e pipeline")
     p.add_argument("--no-library-baseline", action="store_true",
                    help="skip timing one cuBLAS DGEMM per instance (the paper's design)")
+    p.add_argument("--no-gate", action="store_true",
+                   help="skip the local two-spin gate line")
     p.add_argument("--no-herk", action="store_true",
                    help="skip the Hermitian-update line (rho = Psi Psi^H, Sec. 3 shapes)")
     p.add_argument("--no-chain", action="store_true",
@@ -409,6 +411,54 @@ def herk_line(bg, steps: int, warmup: int, S: int = 17, count: int = 128):
     return res
 
 
+def gate_line(bg, fp64_peak, steps: int = 20, S: int = 17, walkers: int = 1024):
+    """The local two-spin gate of Alg. 1 ("Apply Local Gate") on `walkers` complex
+    state vectors of S spins (2 GB for 1024 walkers of 17 spins, well above L2):
+    every step applies a fresh Haar gate per walker on a random neighbouring pair.
+    Algorithmic work per amplitude: 4 complex multiply-adds (32 FP64 flops) and
+    32 bytes (read and write once). The norm of every state is checked after the
+    last step (the gates are unitary)."""
+    import torch
+    rng = np.random.default_rng(23)
+    dim = 1 << S
+    gen = torch.Generator(device="cuda").manual_seed(23)
+    psi = torch.randn(walkers * dim, dtype=torch.complex128, device="cuda", generator=gen)
+    norm0 = psi.view(walkers, dim).abs().pow(2).sum(dim=1).sqrt()
+    z = rng.standard_normal((steps, walkers, 4, 4)) + 1j * rng.standard_normal((steps, walkers, 4, 4))
+    q, r = np.linalg.qr(z)
+    d = np.diagonal(r, axis1=-2, axis2=-1)
+    haar = q * (d / np.abs(d))[..., None, :]
+    # column-major 4 x 4 per walker
+    gates = torch.from_numpy(np.ascontiguousarray(haar.transpose(0, 1, 3, 2))).cuda()
+    sites = torch.from_numpy(rng.integers(0, S - 1, (steps, walkers)).astype(np.int32)).cuda()
+    for t in range(min(3, steps)):
+        bg.apply_local_gate(psi, S, sites[t], gates[t])
+    torch.cuda.synchronize()
+    bg.launch_count(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for t in range(steps):
+        bg.apply_local_gate(psi, S, sites[t], gates[t])
+    e1.record()
+    torch.cuda.synchronize()
+    launches = bg.launch_count(reset=True)
+    bg.check_device_errors()
+    ms = e0.elapsed_time(e1) / steps
+    amps = float(walkers) * dim
+    tflops = 32.0 * amps / (ms * 1e-3) / 1e12
+    gbs = 32.0 * amps / (ms * 1e-3) / 1e9
+    drift = float(((psi.view(walkers, dim).abs().pow(2).sum(dim=1).sqrt() - norm0).abs() / norm0).max())
+    return {"workload": f"{walkers} complex states of {S} spins, a Haar two-spin gate per walker "
+                        f"and step on a random neighbouring pair",
+            "steps": steps, "ms_per_step": ms, "value": amps / (ms * 1e-3) / 1e9,
+            "unit": "G amplitudes/s", "fp64_tflops": tflops, "hbm_gbs": gbs,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": tflops / fp64_peak if fp64_peak else None,
+                         "peak_source": "DFMA probe measured live (bg_probe_fp64_peak)"},
+            "hbm_frac_of_copy_peak": gbs / 6780.0, "gpu_launches": launches,
+            "max_norm_drift": drift}
+
+
 def chain_line(bg, fp64_steps: int = 10, split_steps: int = 200):
     """The annealing-shaped chain: 960 complex walkers of n = 256 and 64 of
     n = 1024, each multiplied by a pool unitary per step (Alg. 1 step loop),
@@ -728,6 +778,11 @@ def main():
         chain = chain_line(bg)
         log(f"chain: {json.dumps(chain)}")
 
+    gate = None
+    if not args.no_gate:
+        gate = gate_line(bg, fp64_peak)
+        log(f"local gate: {json.dumps(gate)}")
+
     herk = None
     if not args.no_herk:
         herk = herk_line(bg, steps=max(2, args.steps // 2), warmup=1)
@@ -758,6 +813,7 @@ def main():
         "library_baseline": lib_base,
         "herk": herk,
         "chain": chain,
+        "gate": gate,
         "peaks_source": pk_src,
     }
     print(json.dumps(line), flush=True)

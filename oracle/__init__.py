@@ -2,8 +2,10 @@
 
 C_i = alpha * A_i * B_i + beta * C_i over N independent instances, in FP64
 and complex128, written out as a plain triple loop in C (``oracle_gemm.c``);
-and the local two-spin gate of the annealing step (Sec. 2, "Apply Local
-Gate") on a batch of state vectors (``oracle_gate.c``).
+the local two-spin gate of the annealing step (Sec. 2, "Apply Local
+Gate") on a batch of state vectors (``oracle_gate.c``); and the entanglement
+entropy of Alg. 1's "Calculate Entropy" (``entanglement_entropy``: the oracle
+GEMM for rho = Psi Psi^H, then numpy's Hermitian eigensolver as a library step).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package. The GPU library never calls it and the
@@ -184,3 +186,26 @@ def two_site_gate(states: np.ndarray, S: int, sites, gates: np.ndarray,
     if bad:
         raise ValueError(f"{bad} walker(s) with a site outside 0..S-2")
     return st
+
+
+def entanglement_entropy(psi: np.ndarray, S: int, split: int | None = None) -> float:
+    """Entanglement entropy of a pure state of S spins across a cut (Sec. 2,
+    Alg. 1 "Calculate Entropy"), following the paper's steps: Psi is the state
+    reshaped to M x K (M = 2^(S - split) rows for the upper spins, K = 2^split
+    columns for the lower ones, split = floor(S/2) by default, Sec. 3's
+    shapes); rho = Psi Psi^H is formed by the oracle GEMM; its eigenvalues
+    (numpy.linalg.eigvalsh, a library step) give p_i = lambda_i / sum(lambda);
+    the entropy is -sum p_i ln p_i over p_i > 0 (natural log).
+    """
+    split = S // 2 if split is None else int(split)
+    M, K = 1 << (S - split), 1 << split
+    psi = np.asarray(psi, dtype=np.complex128).reshape(-1)
+    assert psi.size == M * K
+    # amplitude of basis state x = upper * K + lower sits at row upper, column lower
+    P = psi.reshape(M, K)
+    rho = matmul(P, np.conj(P.T))
+    lam = np.linalg.eigvalsh(rho)
+    total = float(np.sum(lam))
+    p = lam / total
+    p = p[p > 0]
+    return float(-np.sum(p * np.log(p)))

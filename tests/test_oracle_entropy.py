@@ -1,0 +1,77 @@
+"""Pins of the entropy oracle (Sec. 2, Alg. 1 "Calculate Entropy"):
+rho = Psi Psi^H of the state reshaped across the cut, its spectrum, and
+-sum p ln p. The pins use what fixes the entropy without the oracle's route:
+
+* states built from chosen Schmidt coefficients, Psi = U diag(sqrt(p)) V^H
+  with Haar U and V: the entropy is -sum p ln p of the chosen p;
+* product states have entropy 0, maximally entangled ones ln(min(M, K));
+* local unitaries on either side leave it unchanged, and so does the
+  normalisation of the state;
+* the singular values of Psi (numpy's SVD, another library routine) give
+  the same value.
+"""
+import numpy as np
+
+import oracle
+
+
+def haar(rng, n):
+    z = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def from_schmidt(rng, p, M, K):
+    """State whose M x K reshape has squared singular values p (sum 1)."""
+    r = len(p)
+    U = haar(rng, M)[:, :r]
+    V = haar(rng, K)[:, :r]
+    P = U @ np.diag(np.sqrt(p)) @ np.conj(V.T)
+    return P.reshape(-1)
+
+
+def test_schmidt_spectrum_closed_form():
+    rng = np.random.default_rng(60)
+    for S in (2, 5, 8, 11):
+        M, K = 1 << (S - S // 2), 1 << (S // 2)
+        r = min(M, K)
+        p = rng.random(r) ** 3
+        p /= p.sum()
+        psi = from_schmidt(rng, p, M, K)
+        want = float(-np.sum(p * np.log(p)))
+        assert abs(oracle.entanglement_entropy(psi, S) - want) <= 1e-12 * max(1.0, want)
+
+
+def test_product_and_maximally_entangled():
+    rng = np.random.default_rng(61)
+    S = 8
+    M, K = 1 << (S - S // 2), 1 << (S // 2)
+    a = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    b = rng.standard_normal(K) + 1j * rng.standard_normal(K)
+    assert abs(oracle.entanglement_entropy(np.outer(a, b).reshape(-1), S)) <= 1e-12
+    psi = from_schmidt(rng, np.full(min(M, K), 1.0 / min(M, K)), M, K)
+    assert abs(oracle.entanglement_entropy(psi, S) - np.log(min(M, K))) <= 1e-12
+
+
+def test_local_unitaries_and_scale_leave_it_unchanged():
+    rng = np.random.default_rng(62)
+    S = 9
+    M, K = 1 << (S - S // 2), 1 << (S // 2)
+    psi = rng.standard_normal(M * K) + 1j * rng.standard_normal(M * K)
+    s0 = oracle.entanglement_entropy(psi, S)
+    P = psi.reshape(M, K)
+    moved = (haar(rng, M) @ P @ haar(rng, K)).reshape(-1)
+    assert abs(oracle.entanglement_entropy(moved, S) - s0) <= 1e-11
+    assert abs(oracle.entanglement_entropy(3.5 * psi, S) - s0) <= 1e-11
+
+
+def test_matches_singular_values():
+    rng = np.random.default_rng(63)
+    for S, split in ((6, 3), (7, 2), (10, 5)):
+        M, K = 1 << (S - split), 1 << split
+        psi = rng.standard_normal(M * K) + 1j * rng.standard_normal(M * K)
+        sv = np.linalg.svd(psi.reshape(M, K), compute_uv=False)
+        p = sv ** 2 / np.sum(sv ** 2)
+        p = p[p > 0]
+        want = float(-np.sum(p * np.log(p)))
+        assert abs(oracle.entanglement_entropy(psi, S, split) - want) <= 1e-11

@@ -196,6 +196,16 @@ def entanglement_entropy(psi: np.ndarray, S: int, split: int | None = None) -> f
     shapes); rho = Psi Psi^H is formed by the oracle GEMM; its eigenvalues
     (numpy.linalg.eigvalsh, a library step) give p_i = lambda_i / sum(lambda);
     the entropy is -sum p_i ln p_i over p_i > 0 (natural log).
+
+    The cut: spin i is bit i of the basis index x (as for the local gate);
+    the lower spins 0..split-1 (x mod K) index the columns of Psi and the
+    upper spins split..S-1 (x div K) its rows, so the cut lies between spins
+    split-1 and split. In the library's column-major convention the state
+    vector itself is, without a copy, the K x M matrix X = Psi^T (row = lower
+    spins); X X^H = conj(Psi^H Psi) has the nonzero spectrum of rho, which
+    is the route a GPU path takes. (Viewing the vector as a column-major
+    M x K matrix instead would cut between spins S-split-1 and S-split: the
+    same cut only for even S.)
     """
     split = S // 2 if split is None else int(split)
     M, K = 1 << (S - split), 1 << split

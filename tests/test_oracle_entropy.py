@@ -75,3 +75,28 @@ def test_matches_singular_values():
         p = p[p > 0]
         want = float(-np.sum(p * np.log(p)))
         assert abs(oracle.entanglement_entropy(psi, S, split) - want) <= 1e-11
+
+
+def test_cut_position_for_odd_spin_count():
+    """Odd S: the two halvings differ, and the oracle takes the cut between spins
+    split-1 and split (split = floor(S/2); lower spins = low bits of the basis
+    index). A Bell pair on spins 1 and 2 of a 5-spin product state straddles
+    that cut (entropy ln 2) but not the other halving, between spins 2 and 3
+    (entropy 0). Built amplitude by amplitude, without the oracle's route."""
+    rng = np.random.default_rng(64)
+    S = 5
+    one = [rng.standard_normal(2) + 1j * rng.standard_normal(2) for _ in range(3)]
+    one = [v / np.linalg.norm(v) for v in one]
+    psi = np.zeros(1 << S, dtype=np.complex128)
+    for x in range(1 << S):
+        b = [(x >> i) & 1 for i in range(S)]
+        if b[1] == b[2]:
+            psi[x] = one[0][b[0]] * one[1][b[3]] * one[2][b[4]] / np.sqrt(2.0)
+    assert abs(oracle.entanglement_entropy(psi, S) - np.log(2.0)) <= 1e-12
+    # the other halving (3 lower spins) is the product cut
+    assert abs(oracle.entanglement_entropy(psi, S, split=3)) <= 1e-12
+    # the column-major K x M view of the vector is Psi^T: same spectrum of X X^H
+    K, M = 1 << (S // 2), 1 << (S - S // 2)
+    X = psi.reshape(M, K).T
+    lam = np.linalg.eigvalsh(X @ np.conj(X.T))
+    assert np.allclose(np.sort(lam)[-2:], [0.5, 0.5], atol=1e-12)

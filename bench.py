@@ -411,7 +411,8 @@ def herk_line(bg, steps: int, warmup: int, S: int = 17, count: int = 128):
     return res
 
 
-def gate_line(bg, fp64_peak, steps: int = 20, S: int = 17, walkers: int = 1024):
+def gate_line(bg, fp64_peak, hbm_peak, hbm_src, steps: int = 20, S: int = 17,
+              walkers: int = 1024):
     """The local two-spin gate of Alg. 1 ("Apply Local Gate") on `walkers` complex
     state vectors of S spins (2 GB for 1024 walkers of 17 spins, well above L2):
     every step applies a fresh Haar gate per walker on a random neighbouring pair.
@@ -455,7 +456,9 @@ def gate_line(bg, fp64_peak, steps: int = 20, S: int = 17, walkers: int = 1024):
             "roofline": {"bound": "alu", "achieved": tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": tflops / fp64_peak if fp64_peak else None,
                          "peak_source": "DFMA probe measured live (bg_probe_fp64_peak)"},
-            "hbm_frac_of_copy_peak": gbs / 6780.0, "gpu_launches": launches,
+            "hbm_frac_of_copy_peak": gbs / hbm_peak,
+            "hbm_peak": {"value": hbm_peak, "unit": "GB/s", "source": hbm_src},
+            "gpu_launches": launches,
             "max_norm_drift": drift}
 
 
@@ -780,7 +783,7 @@ def main():
 
     gate = None
     if not args.no_gate:
-        gate = gate_line(bg, fp64_peak)
+        gate = gate_line(bg, fp64_peak, pk["hbm_gbs"], f"copy bandwidth, {pk_src} (MEASURED_PEAKS.json)")
         log(f"local gate: {json.dumps(gate)}")
 
     herk = None

@@ -154,10 +154,11 @@ bg_status batched_gemm_fixed(bg_dtype dtype, int64_t m, int64_t n, int64_t k,
  *    with BG_ERR_INVALID_ARG before any work is queued, the message giving
  *    the bytes it needs.
  *  - Set-up: the first call on each device looks up the array's address on
- *    that device (the CUDA runtime loads the module holding it then). Make
- *    that first call before any stream capture.
+ *    that device (the CUDA runtime loads the module holding it then).
  *  - Each call clears what must start at zero (error word, exponent stores)
- *    and uploads its work tables from host memory on `stream`.
+ *    and uploads its work tables from host memory on `stream`. That host
+ *    memory is released on return, so a call made while `stream` is being
+ *    captured into a CUDA graph is refused with BG_ERR_CAPTURE.
  *  - Concurrency: all calls on one device share the one array. Calls queued
  *    on the same stream are ordered and safe; calls whose work overlaps in
  *    time (other streams, other host threads) race on the array and give

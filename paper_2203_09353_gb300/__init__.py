@@ -317,6 +317,40 @@ def unitarity_drift(dtype, d_n, d_off, C, out, count: int, stream=None) -> None:
                                              _ptr(C), _ptr(out), _stream(stream)))
 
 
+def _check_gate_args(states, spins: int, sites, gates, walkers: int, stride: int) -> None:
+    """Argument checks of apply_local_gate for torch tensors (raw integer pointers
+    are passed through unchecked): element types, contiguity, sizes against the
+    walker count and stride, then the device. Raises ValueError before any launch."""
+    import torch
+    tens = {"states": states, "sites": sites, "gates": gates}
+    if not all(isinstance(x, torch.Tensor) for x in tens.values()):
+        return
+    want = {"states": torch.complex128, "sites": torch.int32, "gates": torch.complex128}
+    for name, x in tens.items():
+        if x.dtype != want[name]:
+            raise ValueError(f"apply_local_gate: {name} must be {want[name]}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"apply_local_gate: {name} must be contiguous")
+    if walkers < 0 or walkers > sites.numel():
+        raise ValueError(f"apply_local_gate: {walkers} walkers but {sites.numel()} sites")
+    if gates.numel() < 16 * walkers:
+        raise ValueError(f"apply_local_gate: gates holds {gates.numel()} entries, "
+                         f"{16 * walkers} needed (16 per walker)")
+    if not 2 <= spins <= 40:
+        raise ValueError(f"apply_local_gate: spins = {spins} outside 2..40")
+    if stride < (1 << spins):
+        raise ValueError(f"apply_local_gate: stride {stride} below 2^spins = {1 << spins}")
+    need = (walkers - 1) * stride + (1 << spins) if walkers > 0 else 0
+    if states.numel() < need:
+        raise ValueError(f"apply_local_gate: states holds {states.numel()} amplitudes, "
+                         f"{need} needed")
+    if walkers > 0:
+        cur = torch.cuda.current_device() if torch.cuda.is_available() else None
+        for name, x in tens.items():
+            if not x.is_cuda or x.device.index != cur:
+                raise ValueError(f"apply_local_gate: {name} must be on the current CUDA device")
+
+
 def apply_local_gate(states, spins: int, sites, gates, walkers: int | None = None,
                      stride: int | None = None, stream=None) -> None:
     """The local two-spin gate (Alg. 1, "Apply Local Gate") on device state vectors, in place.
@@ -330,6 +364,7 @@ def apply_local_gate(states, spins: int, sites, gates, walkers: int | None = Non
     stride = (1 << spins) if stride is None else int(stride)
     if walkers is None:
         walkers = int(sites.numel())
+    _check_gate_args(states, int(spins), sites, gates, int(walkers), stride)
     _check(load_library().apply_local_gate(dtype_code("c128"), int(walkers), int(spins),
                                            _ptr(sites), _ptr(gates), _ptr(states), stride,
                                            _stream(stream)))

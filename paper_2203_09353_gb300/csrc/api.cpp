@@ -698,6 +698,12 @@ bg_status batched_gemm_fixed_static(bg_dtype dtype, int64_t m, int64_t n, int64_
                 "batched_gemm_fixed_static runs the split mode only (precision.mode must be "
                 "BG_MODE_SPLIT_BF16)");
   if (empty) return BG_OK;
+  // The call uploads its work tables from host vectors freed on return: a
+  // captured copy would read freed memory when the graph replays.
+  if (stream_capturing(reinterpret_cast<cudaStream_t>(stream)))
+    return fail(BG_ERR_CAPTURE,
+                "batched_gemm_fixed_static uploads host tables on every call; the stream is "
+                "being captured");
   int dev = 0, sms = 0;
   BG_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   BG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");

@@ -133,3 +133,29 @@ def test_gate_argument_checks(gpu):
     bg.launch_count(reset=True)
     assert lib.apply_local_gate(bg.BG_C128, 0, 6, s.data_ptr(), g.data_ptr(), p, 64, None) == 0
     assert bg.launch_count(reset=True) == 0  # no walkers: nothing launched
+
+
+def test_wrapper_rejects_bad_tensors_before_launch(gpu):
+    """The Python binding checks element types and sizes of torch tensors before
+    the call: an int64 sites tensor (torch's default integer type) would be read
+    as int32 halves, and undersized states or gates would be written or read out
+    of bounds. Each raises ValueError and launches nothing."""
+    S, W = 6, 3
+    st = torch.zeros(W << S, dtype=torch.complex128, device="cuda")
+    s32 = torch.zeros(W, dtype=torch.int32, device="cuda")
+    g = torch.zeros(16 * W, dtype=torch.complex128, device="cuda")
+    bad = [
+        dict(states=st, sites=s32.to(torch.int64), gates=g),
+        dict(states=st[: (W << S) - 1], sites=s32, gates=g),
+        dict(states=st, sites=s32, gates=g[: 16 * W - 1]),
+        dict(states=st.to(torch.complex64), sites=s32, gates=g),
+        dict(states=st.view(W, 1 << S).t(), sites=s32, gates=g),
+    ]
+    bg.launch_count(reset=True)
+    for kw in bad:
+        with pytest.raises(ValueError):
+            bg.apply_local_gate(kw["states"], S, kw["sites"], kw["gates"])
+    assert bg.launch_count(reset=True) == 0
+    with pytest.raises(ValueError):
+        bg.apply_local_gate(st, S, s32, g, stride=(1 << S) + 1)  # 3 strides overrun the buffer
+    assert bg.launch_count(reset=True) == 0

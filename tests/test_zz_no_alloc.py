@@ -88,3 +88,24 @@ def test_fp64_mode_is_refused(gpu):
     with pytest.raises(bg.BgemmError) as ei:
         run_static(b, bg.precision("fp64"))
     assert ei.value.status == 1
+
+
+def test_capture_is_refused(gpu):
+    """The call uploads host tables that it frees on return, so a call inside a
+    stream capture is refused (BG_ERR_CAPTURE) before anything is queued."""
+    import torch
+    b, prec = cases()[0]
+    m, n, k, count = b.fixed_shape()
+    A, B, C = dev(b.A), dev(b.B), dev(b.C)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    status = None
+    with torch.cuda.graph(g):
+        try:
+            bg.batched_gemm_fixed_static(b.dtype, m, n, k, b.alpha, A, m, m * k, B, k, k * n,
+                                         b.beta, C, m, m * n, count, prec)
+        except bg.BgemmError as e:
+            status = e.status
+    assert status == 5
+    torch.cuda.synchronize()
+    assert np.array_equal(host(C), b.C)

@@ -94,8 +94,34 @@ def peaks():
     return dict(FALLBACK_PEAKS), "fallback"
 
 
-def make_batch(workload: str, count: int, rank: int):
+def lpt_shard(seed: int, count: int, world: int, rank: int, values: str):
+    """Rank ``rank``'s share of ONE size-mix batch of ``world * count`` instances.
+    The sizes of the whole batch are drawn once from ``seed`` (every rank draws
+    the same ones); the instances are split by the library's longest-first
+    partition of their flops (bg_partition_lpt), which every rank computes
+    identically; the values of this rank's instances are drawn from
+    seed + 1000 rank. Returns (batch, ids of the whole batch this rank holds)."""
+    import paper_2203_09353_gb300 as bg
     from paper_2203_09353_gb300 import synth
+    ns = synth.draw_sizes(np.random.default_rng(seed), world * count)
+    part, _ = bg.partition_lpt(2.0 * ns.astype(np.float64) ** 3, world)
+    ids = np.flatnonzero(part == rank)
+    b = synth.batch_of_sizes(np.random.default_rng(seed + 1000 * rank), ns[ids], values, 1.0, 0.5,
+                             f"size_mix_{values}_{world * count}_part{rank}of{world}")
+    return b, ids
+
+
+def make_batch(workload: str, count: int, rank: int, world: int = 1):
+    from paper_2203_09353_gb300 import synth
+    if workload.startswith("mix-") and world > 1:
+        values = workload[4:]
+        seed = 2 if values == "uniform" else 3
+        b, ids = lpt_shard(seed, count, world, rank, values)
+        return b, (f"part {rank} of {world} (longest-first flop split) of one batch of "
+                   f"{world * count} real FP64 instances n in {{16..512}} (w .3/.25/.2/.15/.07/.03), "
+                   f"{'U[-1,1]' if values == 'uniform' else '|x| = 10^U(-4,4) random sign'}, "
+                   f"alpha=1, beta=0.5, sizes seed {seed}, values seed {seed + 1000 * rank}; "
+                   f"{b.count} instances here")
     if workload == "fixed-n32":
         return synth.fixed_real_n32(), "64 real FP64 instances n=32, U[-1,1], seed 0, C=AB"
     if workload == "complex-n64":
@@ -553,7 +579,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     pk, pk_src = peaks()
-    batch, desc = make_batch(args.workload, args.count, rank)
+    batch, desc = make_batch(args.workload, args.count, rank, world)
     log(f"generated {desc}")
     flops = batch.flops()
     job_flops = sum_over_ranks(pg, flops)  # every rank's shard counts toward the job
@@ -606,6 +632,14 @@ def main():
             bg.rel_err(batch.dtype, dtab, A, B, outs[m], outs["fp64"], errbuf, batch.count)
             e["max_vs_fp64_path_all"] = float(errbuf.max().item())
         errs[m] = e
+    # final scalar reduce over ranks, outside the timed region (the ranks share
+    # nothing on the data path): the whole job's sum of ||C_i||_F^2 of the
+    # headline mode, its instance count and its worst error against the FP64 path
+    job_reduce = {
+        "sum_c_frobenius_sq": sum_over_ranks(pg, float(outs[args.mode].pow(2).sum())),
+        "instances": int(sum_over_ranks(pg, float(batch.count))),
+        "max_err_vs_fp64_path": (max_over_ranks(pg, errs[args.mode]["max_vs_fp64_path_all"])
+                                 if "max_vs_fp64_path_all" in errs[args.mode] else None)}
     del outs
     log("errors: " + json.dumps(errs))
 
@@ -805,12 +839,16 @@ def main():
         "config": {"workload": desc, "mode": head, "count": batch.count,
                    "gflop_per_step_fp64_equiv": flops / 1e9,
                    "l2": "inputs (A, B, C) larger than L2, no flush",
-                   "parallelism": f"{world} independent shard(s), no collective"},
+                   "parallelism": (f"{world} parts of one batch split longest-first by flops, "
+                                   "no collective on the data path" if world > 1 and
+                                   args.workload.startswith("mix-") else
+                                   f"{world} independent replica(s), no collective")},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
+        "job_reduce": job_reduce,
         "modes": res,
         "fp64_peak_tflops_measured": fp64_peak,
         "library_baseline": lib_base,

@@ -245,6 +245,24 @@ void bg_plan_destroy(bg_plan* plan);
 bg_status apply_local_gate(bg_dtype dtype, int64_t walkers, int32_t spins, const int32_t* sites,
                            const void* gates, void* states, int64_t stride, bg_stream_t stream);
 
+/* ---- spreading independent work over GPUs (Sec. 4.B, Table 1) --------------
+ * The paper runs its independent Monte Carlo procedures on several GPUs and
+ * reports near-linear scaling (Sec. 4.B, Table 1). This host-only call splits
+ * `count` independent work items -- GEMM instances of a batch, or whole
+ * walkers of a chain -- with costs host_cost[i] >= 0 (e.g. 2 m n k flops of
+ * an instance, or steps x 8 n^3 for a complex walker) over `parts` processes
+ * by longest processing time first: the items in decreasing cost (equal
+ * costs: lower index first) each go to the part with the smallest load so
+ * far (equal loads: lower part). The result depends only on the inputs, so
+ * every rank computes the same partition. No part's load exceeds the mean
+ * load plus the largest single cost.
+ * host_cost: HOST double [count]; out_part: HOST int32 [count], the part
+ * (0..parts-1) of each item; out_load: HOST double [parts] or NULL, each
+ * part's summed cost. A negative or non-finite cost, parts < 1 or a NULL
+ * array with count > 0 is BG_ERR_INVALID_ARG. No device work. */
+bg_status bg_partition_lpt(int64_t count, const double* host_cost, int32_t parts,
+                           int32_t* out_part, double* out_load);
+
 /* Plan introspection: number of instances, of device work items per grouped
  * call, of kernel launches per grouped call (or per chain step), workspace
  * bytes, and the size classes. */

@@ -39,7 +39,7 @@ EXPORTS = ("batched_gemm_fixed", "batched_gemm_fixed_static", "batched_gemm_plan
            "bg_plan_kernel_times", "bg_rel_err",
            "bg_unitarity_drift", "bg_split_planes", "bg_check_device_errors",
            "bg_test_bounded_wait", "bg_probe_fp64_peak", "bg_launch_count", "bg_status_string",
-           "bg_last_error", "bg_version", "apply_local_gate")
+           "bg_last_error", "bg_version", "apply_local_gate", "bg_partition_lpt")
 
 
 class BgemmError(RuntimeError):
@@ -96,6 +96,7 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "bg_test_bounded_wait": [i64, vp],
         "bg_probe_fp64_peak": [i32, P(dbl), vp],
         "apply_local_gate": [i32, i64, i32, vp, vp, vp, i64, vp],
+        "bg_partition_lpt": [i64, P(dbl), i32, P(i32), P(dbl)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -368,6 +369,26 @@ def apply_local_gate(states, spins: int, sites, gates, walkers: int | None = Non
     _check(load_library().apply_local_gate(dtype_code("c128"), int(walkers), int(spins),
                                            _ptr(sites), _ptr(gates), _ptr(states), stride,
                                            _stream(stream)))
+
+
+def partition_lpt(costs, parts: int) -> tuple[np.ndarray, np.ndarray]:
+    """Longest-processing-time-first split of independent items over ``parts``
+    processes (C ABI bg_partition_lpt): returns (part of each item, load per part)."""
+    c = np.ascontiguousarray(costs, dtype=np.float64).reshape(-1)
+    part = np.zeros(c.size, dtype=np.int32)
+    load = np.zeros(max(1, int(parts)), dtype=np.float64)
+    P = ctypes.POINTER
+    _check(load_library().bg_partition_lpt(c.size, c.ctypes.data_as(P(ctypes.c_double)),
+                                           int(parts), part.ctypes.data_as(P(ctypes.c_int32)),
+                                           load.ctypes.data_as(P(ctypes.c_double))))
+    return part, load[:int(parts)]
+
+
+def instance_flops(table, dtype) -> np.ndarray:
+    """Algorithmic flops per instance of a bg_instance table: 2 m n k (8 m n k complex)."""
+    t = np.asarray(table, dtype=np.int64).reshape(-1, 9).astype(np.float64)
+    per = 8.0 if dtype_code(dtype) == BG_C128 else 2.0
+    return per * t[:, 0] * t[:, 1] * t[:, 2]
 
 
 def split_planes(m, k, X, ldx, axis, slices, beta_bits, exps, digits, stream=None) -> None:

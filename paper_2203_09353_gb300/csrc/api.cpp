@@ -1204,6 +1204,44 @@ bg_status bg_probe_fp64_peak(int32_t mma_kind, double* tflops, bg_stream_t strea
   return BG_OK;
 }
 
+bg_status bg_partition_lpt(int64_t count, const double* host_cost, int32_t parts,
+                           int32_t* out_part, double* out_load) {
+  if (count < 0) return fail(BG_ERR_INVALID_ARG, "negative count");
+  if (parts < 1) return fail(BG_ERR_INVALID_ARG, "parts must be >= 1");
+  if (count > 0 && (!host_cost || !out_part))
+    return fail(BG_ERR_INVALID_ARG, "host_cost and out_part must not be NULL");
+  for (int64_t i = 0; i < count; ++i)
+    if (!(host_cost[i] >= 0.0) || std::isinf(host_cost[i]))
+      return fail(BG_ERR_INVALID_ARG, "cost %lld is negative or not finite", (long long)i);
+  // longest first; equal costs keep the lower index first
+  std::vector<int64_t> order((size_t)count);
+  for (int64_t i = 0; i < count; ++i) order[(size_t)i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t a, int64_t b) { return host_cost[a] > host_cost[b]; });
+  // min-heap of (load, part): the least loaded part, the lower index on ties
+  using Slot = std::pair<double, int32_t>;
+  std::vector<Slot> heap;
+  heap.reserve((size_t)parts);
+  for (int32_t r = 0; r < parts; ++r) heap.push_back({0.0, r});
+  auto later = [](const Slot& a, const Slot& b) {
+    return a.first > b.first || (a.first == b.first && a.second > b.second);
+  };
+  std::make_heap(heap.begin(), heap.end(), later);
+  std::vector<double> load((size_t)parts, 0.0);
+  for (int64_t i : order) {
+    std::pop_heap(heap.begin(), heap.end(), later);
+    Slot s = heap.back();
+    out_part[i] = s.second;
+    s.first += host_cost[i];
+    load[(size_t)s.second] = s.first;
+    heap.back() = s;
+    std::push_heap(heap.begin(), heap.end(), later);
+  }
+  if (out_load)
+    for (int32_t r = 0; r < parts; ++r) out_load[r] = load[(size_t)r];
+  return BG_OK;
+}
+
 int64_t bg_launch_count(int32_t reset) {
   const int64_t v = g_launches;
   if (reset) g_launches = 0;

@@ -230,6 +230,14 @@ def mixed_batch(seed: int, count: int, values: str, alpha=1.0, beta=0.5, sizes=S
     """
     rng = np.random.default_rng(seed)
     ns = draw_sizes(rng, count, sizes, weights)
+    return batch_of_sizes(rng, ns, values, alpha, beta,
+                          name or f"mixed_{values}_{count}_seed{seed}")
+
+
+def batch_of_sizes(rng, ns, values: str, alpha=1.0, beta=0.5, name: str = "sized") -> Batch:
+    """Square real instances of the given sizes, packed, values drawn from ``rng``
+    (A, then B, then C, as in ``mixed_batch``)."""
+    ns = np.asarray(ns, dtype=np.int64)
     table, la, lb, lc = pack_table([(int(n), int(n), int(n)) for n in ns])
     out = []
     for length, (rows, cols, ld, off) in ((la, (0, 2, 3, 6)), (lb, (2, 1, 4, 7)),
@@ -244,8 +252,8 @@ def mixed_batch(seed: int, count: int, values: str, alpha=1.0, beta=0.5, sizes=S
             X[~_gap_mask(table, length, rows, cols, ld, off)] = 0.0
         out.append(X)
     A, B, C = out
-    return Batch(name or f"mixed_{values}_{count}_seed{seed}", "r64", table, A, B, C, alpha,
-                 beta, meta={"sizes": ns})
+    return Batch(name, "r64", table, A, B, C, alpha, beta, meta={"sizes": ns})
+
 
 
 def size_mix_uniform(count: int = 20000) -> Batch:

@@ -441,7 +441,7 @@ static int level_pass(int s, int beta) {
 
 struct SplitPlan {
   bg_dtype dt = BG_R64;
-  int s = 0, beta = 0, bn = 0, kpass = 0, a_stages = 0;
+  int s = 0, beta = 0, bn = 0, kpass = 0, a_groups = 0;
   size_t smem = 0;
   bool chain = false;
   bool herk = false;       // Hermitian rank-k updates (B = A^H, lower triangle)
@@ -534,12 +534,13 @@ static bool setup_common(SplitPlan* p, bg_dtype dt, const bg_precision& pr, int 
   }
   const size_t bbytes = 2 * (size_t)p->s * p->bn * kLineBytes;
   const size_t budget = kMaxDynSmem - 1024 - sizeof(GemmBars);
-  p->a_stages = (int)std::min<size_t>(kMaxAStages, (budget - bbytes) / kATileBytes);
-  if (p->a_stages < 2) {
+  p->a_groups =
+      (int)std::min<size_t>(kMaxAGroups, (budget - bbytes) / ((size_t)kAGroup * kATileBytes));
+  if (p->a_groups < 2) {
     *err = "split mode: shared memory too small for this slice count";
     return false;
   }
-  p->smem = 1024 + bbytes + (size_t)p->a_stages * kATileBytes + sizeof(GemmBars);
+  p->smem = 1024 + bbytes + (size_t)p->a_groups * kAGroup * kATileBytes + sizeof(GemmBars);
   return true;
 }
 
@@ -751,9 +752,9 @@ static void finish_desc(SplitPlan* p) {
   char buf[512];
   snprintf(buf, sizeof buf,
            "{\"slices\": %d, \"beta_bits\": %d, \"pairs\": %d, \"tile\": [%d, %d, %d], "
-           "\"kpass_kblocks\": %d, \"a_stages\": %d, \"smem_bytes\": %zu, \"units\": %lld, "
+           "\"kpass_kblocks\": %d, \"a_ring_groups\": %d, \"smem_bytes\": %zu, \"units\": %lld, "
            "\"slice_jobs\": %lld, \"workspace_bytes\": %lld}",
-           p->s, p->beta, p->s * (p->s + 1) / 2, BM, p->bn, BK, p->kpass, p->a_stages, p->smem,
+           p->s, p->beta, p->s * (p->s + 1) / 2, BM, p->bn, BK, p->kpass, p->a_groups, p->smem,
            (long long)p->n_units, (long long)p->n_jobs, (long long)p->bytes);
   p->desc = buf;
 }
@@ -868,7 +869,7 @@ static cudaError_t launch_gemm(SplitPlan* p, void* C, const Scalars& sc, const i
   g.skip_product = sc.alpha_zero;
   g.herk = p->herk ? 1 : 0;
   g.kpass = p->kpass;
-  g.a_stages = p->a_stages;
+  g.a_groups = p->a_groups;
   g.err = d_err;
   cudaError_t e = g.cplx ? launch_split_gemm_c128(p->s, p->grid_gemm, p->smem, st, g)
                          : launch_split_gemm_r64(p->s, p->grid_gemm, p->smem, st, g);

@@ -15,7 +15,13 @@ namespace splitk {
 constexpr int BM = 128, BK = 64;
 constexpr int kATileBytes = BM * BK * 2;  // 16 KiB: one A plane of one k-block
 constexpr int kLineBytes = BK * 2;        // 128 bytes: one row of a tile
-constexpr int kMaxAStages = 8;
+// The A ring holds groups of kAGroup plane slots: the producer fills a group
+// with one barrier and the MMA issuer waits on it once and releases it with
+// one commit. Each wait, fence and commit in the MMA issue loop stalls the
+// tensor pipe for about a hundred clocks (measured on GB300), so one sync
+// per plane held a 9-slice k-block about 40% above its MMA time.
+constexpr int kAGroup = 3;
+constexpr int kMaxAGroups = 4;
 // Split GEMM CTA: producer warp, MMA warp, then 4 H epilogue warps.
 __host__ __device__ constexpr int gemm_threads(int h) { return 64 + 128 * h; }
 constexpr int kMetaStride = 264;  // int32 per block: e[128], R[128] (then padding)
@@ -107,7 +113,7 @@ struct GemmArgs {
   Scalars sc;
   int cplx, s, beta, skip_product;
   int kpass;                  // k-blocks per exact pass
-  int a_stages;               // slots of the A ring
+  int a_groups;               // groups of kAGroup slots in the A ring
   int herk;                   // Hermitian update: store only the lower triangle
   int* err;
 };
@@ -462,9 +468,9 @@ __device__ __forceinline__ double valB(const double* B, const SInst& in, int cpl
 struct GemmBars {
   uint64_t b_full[2];
   uint64_t b_empty[2];
-  uint64_t a_full[kMaxAStages];
-  uint64_t a_empty[kMaxAStages];
-  uint64_t lvl_full[kMaxSlices];
+  uint64_t a_full[kMaxAGroups];   // A ring group g holds its planes
+  uint64_t a_empty[kMaxAGroups];  // the MMAs are done with A ring group g
+  uint64_t lvl_full[kMaxSlices];  // entry i: the levels of plane group i are complete
   uint64_t acc_full[2];   // double-buffered TMEM: accumulator copy b holds a finished tile
   uint64_t acc_empty[2];  // double-buffered TMEM: the epilogue has emptied copy b
   uint64_t tmem_free;

@@ -95,18 +95,19 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
   const int s = SF > 0 ? SF : g.s;
   const int bplanes_bytes = s * BTILE;
   uint8_t* bbuf = smem;                          // 2 x s B tiles
-  uint8_t* aring = smem + 2 * bplanes_bytes;     // a_stages x 16 KiB
-  GemmBars& S = *reinterpret_cast<GemmBars*>(aring + g.a_stages * kATileBytes);
+  uint8_t* aring = smem + 2 * bplanes_bytes;     // a_groups x kAGroup x 16 KiB
+  GemmBars& S = *reinterpret_cast<GemmBars*>(aring + g.a_groups * kAGroup * kATileBytes);
   volatile int* abort_flag = &S.abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int NA = g.a_stages;
+  const int NG = g.a_groups;
+  const int ngroups = (s + kAGroup - 1) / kAGroup;  // plane groups per k-block
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
       mbar_init(&S.b_full[i], 1);
       mbar_init(&S.b_empty[i], 1);
     }
-    for (int i = 0; i < NA; ++i) {
+    for (int i = 0; i < NG; ++i) {
       mbar_init(&S.a_full[i], 1);
       mbar_init(&S.a_empty[i], 1);
     }
@@ -133,9 +134,9 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
 
   if (warp == 0) {
     // ---------------- producer: one TMA bulk copy of the s B planes per k-block, and
-    // the s A planes of the k-block through the A ring
+    // the s A planes of the k-block through the A ring, kAGroup planes per group
     if (lane == 0) {
-      uint32_t kbc = 0, afill = 0;
+      uint32_t kbc = 0, gfill = 0;
       bool ok = true;
       for (int64_t u = blockIdx.x; u < g.nunits && ok; u += gridDim.x) {
         const SplitUnit U = g.units[u];
@@ -157,19 +158,21 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
             mbar_arrive_expect_tx(&S.b_full[buf], (uint32_t)bplanes_bytes);
             bulk_g2s(bbuf + buf * bplanes_bytes, g.tilesB + (bt + (int64_t)kb * s) * BTILE,
                      (uint32_t)bplanes_bytes, &S.b_full[buf]);
-            for (int p = 0; p < s; ++p, ++afill) {
-              const int slot = afill % NA;
-              const uint32_t ause = afill / NA;
-              if (ause > 0 && !mbar_wait(&S.a_empty[slot], (ause - 1) & 1, abort_flag)) {
+            for (int gi = 0; gi < ngroups; ++gi, ++gfill) {
+              const int grp = gfill % NG;
+              const uint32_t guse = gfill / NG;
+              const int p0 = gi * kAGroup, gs = min(kAGroup, s - p0);
+              if (guse > 0 && !mbar_wait(&S.a_empty[grp], (guse - 1) & 1, abort_flag)) {
                 record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_EMPTY_BARRIER, (int)u);
                 *abort_flag = 1;
                 ok = false;
                 break;
               }
-              mbar_arrive_expect_tx(&S.a_full[slot], kATileBytes);
-              bulk_g2s(aring + slot * kATileBytes,
-                       g.tilesA + (at + (int64_t)kb * s + p) * kATileBytes, kATileBytes,
-                       &S.a_full[slot]);
+              mbar_arrive_expect_tx(&S.a_full[grp], (uint32_t)(gs * kATileBytes));
+              for (int j = 0; j < gs; ++j)
+                bulk_g2s(aring + (grp * kAGroup + j) * kATileBytes,
+                         g.tilesA + (at + (int64_t)kb * s + p0 + j) * kATileBytes, kATileBytes,
+                         &S.a_full[grp]);
             }
           }
         }
@@ -177,15 +180,15 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
       // let every copy this thread started land before the CTA can exit
       for (uint32_t j = kbc > 2 ? kbc - 2 : 0; j < kbc; ++j)
         mbar_wait_time(&S.b_full[j & 1], (j >> 1) & 1);
-      for (uint32_t j = afill > (uint32_t)NA ? afill - NA : 0; j < afill; ++j)
-        mbar_wait_time(&S.a_full[j % NA], (j / NA) & 1);
+      for (uint32_t j = gfill > (uint32_t)NG ? gfill - NG : 0; j < gfill; ++j)
+        mbar_wait_time(&S.a_full[j % NG], (j / NG) & 1);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer: one N-concatenated MMA per A plane and K-step
     if (lane == 0) {
       uint32_t kbc = 0, passc = 0;
-      int slot = 0;
-      uint32_t aphase = 0;
+      int grp = 0;
+      uint32_t gphase = 0;
       bool ok = true;
       const uint32_t bbase = smem_u32(bbuf);
       const uint32_t abase = smem_u32(aring);
@@ -228,14 +231,17 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
 #pragma unroll
             for (int p = 0; p < (SF > 0 ? SF : kMaxSlices); ++p) {
               if (SF == 0 && p >= s) break;
-              if (!mbar_wait(&S.a_full[slot], aphase, abort_flag)) {
-                record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_FULL_BARRIER, (int)u);
-                *abort_flag = 1;
-                ok = false;
-                break;
+              const int j = p % kAGroup;  // plane within its ring group
+              if (j == 0) {
+                if (!mbar_wait(&S.a_full[grp], gphase, abort_flag)) {
+                  record_error(g.err, BG_ERR_TIMEOUT, ERRLOC_SPLIT_FULL_BARRIER, (int)u);
+                  *abort_flag = 1;
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
               }
-              tc_fence_after();
-              const uint64_t adesc = sw128_desc(abase + slot * kATileBytes);
+              const uint64_t adesc = sw128_desc(abase + (grp * kAGroup + j) * kATileBytes);
               // B planes 1..s-p (levels p+2 .. s+1) as one N range, cut in pieces of <= 256
               const int ncat = (s - p) * BN;
               const int n1 = ncat > 256 ? ncat - 256 : 0;
@@ -252,11 +258,15 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
                 }
               }
               acc0 = 1u;
-              umma_commit(&S.a_empty[slot]);
-              if (!DB && last_kb) umma_commit(&S.lvl_full[p]);  // level p+2 is complete
-              if (++slot == NA) {
-                slot = 0;
-                aphase ^= 1;
+              if (j == kAGroup - 1 || p == s - 1) {
+                // the group's planes are done: release its slots; in the last k-block of
+                // the pass every level up to p is complete
+                umma_commit(&S.a_empty[grp]);
+                if (!DB && last_kb) umma_commit(&S.lvl_full[p / kAGroup]);
+                if (++grp == NG) {
+                  grp = 0;
+                  gphase ^= 1;
+                }
               }
             }
             if (!ok) break;
@@ -410,10 +420,9 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
             for (int lv = 0; lv < s;) {
               const int nlv = (pairs && lv + 1 < s) ? 2 : 1;
               bool got = true;
-              if (lane == 0) {
-                got = mbar_wait(&S.lvl_full[lv], passc & 1, abort_flag);
-                if (got && nlv == 2) got = mbar_wait(&S.lvl_full[lv + 1], passc & 1, abort_flag);
-              }
+              // level t is complete once its plane group (t / kAGroup) is
+              if (lane == 0)
+                got = mbar_wait(&S.lvl_full[(lv + nlv - 1) / kAGroup], passc & 1, abort_flag);
               got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
               if (!got) {
                 if (lane == 0) {

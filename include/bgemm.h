@@ -245,6 +245,39 @@ void bg_plan_destroy(bg_plan* plan);
 bg_status apply_local_gate(bg_dtype dtype, int64_t walkers, int32_t spins, const int32_t* sites,
                            const void* gates, void* states, int64_t stride, bg_stream_t stream);
 
+/* ---- entanglement entropy (Alg. 1, "Calculate Entropy"; Sec. 3) -----------
+ * Each Monte Carlo step of the paper computes the entanglement entropy of the
+ * new state: the state is reshaped across a cut of the chain, multiplied by
+ * its own conjugate transpose (the GEMM of Sec. 3, with the shapes M = 2^(S -
+ * floor(S/2)), K = 2^floor(S/2)), and the eigenvalues p_i of the normalised
+ * density matrix give S = -sum_i p_i ln p_i.
+ *  - The cut: spin i is bit i of the basis index x (as for apply_local_gate);
+ *    the lower `split` spins (x mod K, K = 2^split) are one side, the upper
+ *    spins (x div K, M = 2^(spins - split) values) the other. The state
+ *    vector of walker w is, without a copy, the column-major K x M matrix X_w
+ *    (leading dimension K), and G_w = X_w X_w^H (K x K) has the nonzero
+ *    eigenvalues of rho_w = Psi Psi^H. p_i = lambda_i(G_w) / sum_j lambda_j.
+ *  - entropy_plan: `walkers` complex128 states of 2^spins amplitudes, walker w
+ *    at element w * stride (stride >= 2^spins); 2 <= spins <= 30,
+ *    1 <= split <= min(spins - 1, 11). precision (NULL = FP64) selects the
+ *    precision of G_w: it is formed by a Hermitian-update plan
+ *    (BG_PLAN_HERK) in that mode. The eigenvalues are always computed in
+ *    FP64: Householder reduction of G_w to a real tridiagonal matrix, then
+ *    bisection on its Sturm sequence. flags: 0 or BG_PLAN_PROFILE (slot 0 of
+ *    bg_plan_kernel_times: G; slot 1: the eigenvalues and the entropy). The
+ *    plan owns a workspace of walkers x K x K complex128 plus 2 walkers x K
+ *    doubles (bg_plan_get_info). Must not be called during stream capture.
+ *  - batched_entropy: states: DEVICE, 16-byte aligned; entropy: DEVICE
+ *    double [walkers] (natural logarithm); eigenvalues: DEVICE double
+ *    [walkers][K] or NULL: the K eigenvalues of each G_w, ascending, not
+ *    normalised. Asynchronous on `stream`; calls on one plan must not overlap. */
+bg_status entropy_plan(bg_plan** out, int64_t walkers, int32_t spins, int32_t split,
+                       int64_t stride, const bg_precision* precision, uint32_t flags,
+                       bg_stream_t stream);
+
+bg_status batched_entropy(const bg_plan* plan, const void* states, double* entropy,
+                          double* eigenvalues, bg_stream_t stream);
+
 /* ---- spreading independent work over GPUs (Sec. 4.B, Table 1) --------------
  * The paper runs its independent Monte Carlo procedures on several GPUs and
  * reports near-linear scaling (Sec. 4.B, Table 1). This host-only call splits

@@ -39,7 +39,8 @@ EXPORTS = ("batched_gemm_fixed", "batched_gemm_fixed_static", "batched_gemm_plan
            "bg_plan_kernel_times", "bg_rel_err",
            "bg_unitarity_drift", "bg_split_planes", "bg_check_device_errors",
            "bg_test_bounded_wait", "bg_probe_fp64_peak", "bg_launch_count", "bg_status_string",
-           "bg_last_error", "bg_version", "apply_local_gate", "bg_partition_lpt")
+           "bg_last_error", "bg_version", "apply_local_gate", "bg_partition_lpt",
+           "entropy_plan", "batched_entropy")
 
 
 class BgemmError(RuntimeError):
@@ -97,6 +98,8 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "bg_probe_fp64_peak": [i32, P(dbl), vp],
         "apply_local_gate": [i32, i64, i32, vp, vp, vp, i64, vp],
         "bg_partition_lpt": [i64, P(dbl), i32, P(i32), P(dbl)],
+        "entropy_plan": [P(vp), i64, i32, i32, i64, P(Precision), u32, vp],
+        "batched_entropy": [vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -304,6 +307,35 @@ def chain_step(plan: Plan, U_pool, U_index, C_ping, C_pong, steps: int, stream=N
     lib = load_library()
     _check(lib.chain_step(plan.handle, _ptr(U_pool), _ptr(U_index), _ptr(C_ping), _ptr(C_pong),
                           int(steps), _stream(stream)))
+
+
+def entropy_plan(walkers: int, spins: int, split: int | None = None, stride: int | None = None,
+                 prec: Precision | None = None, flags: int = 0, stream=None) -> Plan:
+    """Plan for the entanglement entropy of ``walkers`` complex128 states of ``spins``
+    spins, cut after the lower ``split`` spins (default floor(spins/2)) (C ABI entropy_plan)."""
+    split = spins // 2 if split is None else int(split)
+    stride = (1 << spins) if stride is None else int(stride)
+    h = ctypes.c_void_p()
+    _check(load_library().entropy_plan(ctypes.byref(h), int(walkers), int(spins), split, stride,
+                                       ctypes.byref(prec) if prec is not None else None,
+                                       int(flags), _stream(stream)))
+    return Plan(h.value, BG_C128, "entropy")
+
+
+def batched_entropy(plan: Plan, states, entropy, eigenvalues=None, stream=None) -> None:
+    """Entropy of every walker's state into the float64 device tensor ``entropy``
+    (optionally the ascending Gram eigenvalues into ``eigenvalues``) (C ABI batched_entropy)."""
+    import torch
+    tens = {"states": states, "entropy": entropy, "eigenvalues": eigenvalues}
+    want = {"states": torch.complex128, "entropy": torch.float64, "eigenvalues": torch.float64}
+    for name, x in tens.items():
+        if isinstance(x, torch.Tensor):
+            if x.dtype != want[name]:
+                raise ValueError(f"batched_entropy: {name} must be {want[name]}, got {x.dtype}")
+            if not x.is_contiguous():
+                raise ValueError(f"batched_entropy: {name} must be contiguous")
+    _check(load_library().batched_entropy(plan.handle, _ptr(states), _ptr(entropy),
+                                          _ptr(eigenvalues), _stream(stream)))
 
 
 def rel_err(dtype, d_table, A, B, C_test, C_ref, out, count: int, stream=None) -> None:

@@ -210,6 +210,14 @@ struct bg_plan {
   int64_t* d_pool_n = nullptr;
   // split path
   SplitPlan* split = nullptr;
+  // entropy plans (Alg. 1, Calculate Entropy): the Gram matrices' HERK plan,
+  // the Gram buffer and the tridiagonal matrices of every walker
+  bool is_entropy = false;
+  bg_plan* gram = nullptr;
+  double2* d_gram = nullptr;
+  double* d_tri_d = nullptr;
+  double* d_tri_e = nullptr;
+  int ent_n = 0;
   // graph cache
   cudaGraphExec_t gexec = nullptr;
   std::vector<uintptr_t> gkey;
@@ -506,6 +514,10 @@ void destroy_plan(bg_plan* p) {
   cudaFree(p->d_pool_off);
   cudaFree(p->d_pool_n);
   if (p->split) split_plan_destroy(p->split);
+  if (p->gram) destroy_plan(p->gram);
+  cudaFree(p->d_gram);
+  cudaFree(p->d_tri_d);
+  cudaFree(p->d_tri_e);
   cudaSetDevice(cur);
   delete p;
 }
@@ -805,6 +817,7 @@ bg_status batched_gemm_grouped(const bg_plan* plan, const void* A_base, const vo
                                bg_stream_t stream) {
   if (!plan) return fail(BG_ERR_INVALID_ARG, "plan is NULL");
   if (plan->is_chain) return fail(BG_ERR_INVALID_ARG, "chain plans run through chain_step");
+  if (plan->is_entropy) return fail(BG_ERR_INVALID_ARG, "entropy plans run through batched_entropy");
   if (plan->count == 0) return BG_OK;
   if (!alpha || !beta) return fail(BG_ERR_INVALID_ARG, "alpha and beta must be host pointers");
   const Scalars sc = make_scalars(plan->dtype, alpha, beta);
@@ -1201,6 +1214,96 @@ bg_status bg_probe_fp64_peak(int32_t mma_kind, double* tflops, bg_stream_t strea
   cudaError_t e = run_fp64_peak_probe(mma_kind, ctx->sms, tflops,
                                       reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "FP64 peak probe");
+  return BG_OK;
+}
+
+bg_status entropy_plan(bg_plan** out, int64_t walkers, int32_t spins, int32_t split,
+                       int64_t stride, const bg_precision* precision, uint32_t flags,
+                       bg_stream_t stream) {
+  if (!out) return fail(BG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  bg_precision pr;
+  bg_status s = check_precision(precision, &pr);
+  if (s != BG_OK) return s;
+  if (walkers < 0 || walkers > 65535)
+    return fail(BG_ERR_INVALID_ARG, "walkers = %lld outside 0..65535", (long long)walkers);
+  if (spins < 2 || spins > 30) return fail(BG_ERR_INVALID_ARG, "spins = %d outside 2..30", spins);
+  if (split < 1 || split > spins - 1 || split > 11)
+    return fail(BG_ERR_INVALID_ARG, "split = %d outside 1..min(spins - 1, 11)", split);
+  if (stride < ((int64_t)1 << spins))
+    return fail(BG_ERR_INVALID_ARG, "stride %lld below 2^spins", (long long)stride);
+  if (flags & ~(uint32_t)BG_PLAN_PROFILE)
+    return fail(BG_ERR_INVALID_ARG, "entropy plans take BG_PLAN_PROFILE only");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (stream_capturing(st))
+    return fail(BG_ERR_CAPTURE, "entropy_plan allocates; the stream is being captured");
+  DeviceCtx* ctx;
+  if ((s = get_ctx(&ctx)) != BG_OK) return s;
+  const int64_t K = (int64_t)1 << split, M = (int64_t)1 << (spins - split);
+  // walker w: X = its state as a column-major K x M matrix; G = X X^H (K x K)
+  std::vector<bg_instance> table((size_t)walkers);
+  for (int64_t w = 0; w < walkers; ++w)
+    table[(size_t)w] = bg_instance{K, K, M, K, M, K, w * stride, 0, w * K * K};
+  bg_plan* p = new bg_plan();
+  p->device = ctx->device;
+  p->dtype = BG_C128;
+  p->prec = pr;
+  p->flags = flags;
+  p->count = walkers;
+  p->is_entropy = true;
+  p->ent_n = (int)K;
+  if (walkers > 0) {
+    s = batched_gemm_plan(&p->gram, BG_C128, walkers, table.data(), &pr, BG_PLAN_HERK, nullptr,
+                          stream);
+    if (s != BG_OK) {
+      destroy_plan(p);
+      return s;
+    }
+    const size_t gb = (size_t)walkers * K * K * sizeof(double2);
+    const size_t tb = (size_t)walkers * K * sizeof(double);
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->d_gram, gb)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_tri_d, tb)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_tri_e, tb)) != cudaSuccess) {
+      destroy_plan(p);
+      return cuda_fail(e, "entropy plan workspace");
+    }
+    p->workspace_bytes = p->gram->workspace_bytes + (int64_t)(gb + 2 * tb);
+    p->launches_per_call = p->gram->launches_per_call + 2;
+  }
+  *out = p;
+  return BG_OK;
+}
+
+bg_status batched_entropy(const bg_plan* plan, const void* states, double* entropy,
+                          double* eigenvalues, bg_stream_t stream) {
+  if (!plan) return fail(BG_ERR_INVALID_ARG, "plan is NULL");
+  if (!plan->is_entropy) return fail(BG_ERR_INVALID_ARG, "not an entropy plan");
+  if (plan->count == 0) return BG_OK;
+  if (!states || !entropy) return fail(BG_ERR_INVALID_ARG, "null device pointer");
+  if (reinterpret_cast<uintptr_t>(states) % 16 != 0)
+    return fail(BG_ERR_INVALID_ARG, "states must be 16-byte aligned");
+  if (fault_injected()) return fail(BG_ERR_CUDA, "injected launch failure (BGEMM_FAULT)");
+  bg_plan* p = const_cast<bg_plan*>(plan);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t* ev = nullptr;
+  if (p->flags & BG_PLAN_PROFILE) {
+    if (p->prof_used == p->prof_events.size()) {
+      std::array<cudaEvent_t, 3> tev{};
+      for (auto& e : tev) BG_CUDA(cudaEventCreate(&e), "profiling event");
+      p->prof_events.push_back(tev);
+    }
+    ev = p->prof_events[p->prof_used++].data();
+    BG_CUDA(cudaEventRecord(ev[0], st), "profiling event record");
+  }
+  const double one[2] = {1.0, 0.0}, zero[2] = {0.0, 0.0};
+  bg_status s = batched_gemm_grouped(p->gram, states, nullptr, p->d_gram, one, zero, stream);
+  if (s != BG_OK) return s;
+  if (ev) BG_CUDA(cudaEventRecord(ev[1], st), "profiling event record");
+  cudaError_t e = launch_entropy_eig(p->d_gram, p->count, p->ent_n, p->d_tri_d, p->d_tri_e,
+                                     entropy, eigenvalues, st);
+  if (e != cudaSuccess) return cuda_fail(e, "entropy eigenvalue launch");
+  if (ev) BG_CUDA(cudaEventRecord(ev[2], st), "profiling event record");
   return BG_OK;
 }
 

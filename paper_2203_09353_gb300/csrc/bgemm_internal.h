@@ -116,4 +116,10 @@ size_t static_scratch_capacity();
 // Address of the static scratch on the current device (looked up once per device).
 bg_status static_scratch(void** out, size_t* bytes, std::string* err);
 
+// Tridiagonalisation and eigenvalues of each walker's Hermitian n x n Gram
+// matrix (lower triangle, overwritten), then the entanglement entropy
+// (entropy.cu). eigs: optional device [walkers][n], ascending.
+cudaError_t launch_entropy_eig(double2* gram, int64_t walkers, int n, double* d, double* e,
+                               double* entropy, double* eigs, cudaStream_t st);
+
 }  // namespace bg

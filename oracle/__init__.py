@@ -5,7 +5,9 @@ and complex128, written out as a plain triple loop in C (``oracle_gemm.c``);
 the local two-spin gate of the annealing step (Sec. 2, "Apply Local
 Gate") on a batch of state vectors (``oracle_gate.c``); and the entanglement
 entropy of Alg. 1's "Calculate Entropy" (``entanglement_entropy``: the oracle
-GEMM for rho = Psi Psi^H, then numpy's Hermitian eigensolver as a library step).
+GEMM for rho = Psi Psi^H, then numpy's Hermitian eigensolver as a library step);
+the Metropolis decision of Alg. 1's "M.A" (``metropolis_accept``) and one
+whole annealing step built from these (``anneal_step``).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package. The GPU library never calls it and the
@@ -219,3 +221,48 @@ def entanglement_entropy(psi: np.ndarray, S: int, split: int | None = None) -> f
     p = lam / total
     p = p[p > 0]
     return float(-np.sum(p * np.log(p)))
+
+
+def metropolis_accept(e_cur, e_new, u, temperature: float, direction: int = 1, *,
+                      _mutant: int = 0) -> np.ndarray:
+    """The Metropolis decision of Alg. 1 ("M.A"), per walker, in FP64.
+
+    The move from energy e_cur to e_new is accepted when it does not raise the
+    energy, delta = direction * (e_new - e_cur) <= 0, and otherwise with
+    probability exp(-delta / T): accepted when u < exp(-delta / T) for the
+    walker's uniform u in [0, 1). direction = +1 lowers the energy (here the
+    entanglement entropy), -1 raises it. T = 0 accepts only moves with
+    delta <= 0; a NaN energy is never accepted. ``_mutant`` plants a mistake
+    for the pin tests only (1: sign of delta flipped, 2: T ignored, 3: delta = 0
+    treated as uphill, 4: the comparison with u reversed).
+    """
+    e_cur = np.asarray(e_cur, dtype=np.float64)
+    e_new = np.asarray(e_new, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    T = float(temperature)
+    delta = float(direction) * (e_new - e_cur)
+    if _mutant == 1:
+        delta = -delta
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        x = -delta if _mutant == 2 else -delta / T
+        thresh = np.exp(x)
+    down = delta < 0 if _mutant == 3 else delta <= 0
+    up = u >= thresh if _mutant == 4 else u < thresh
+    return down | (~down & up)
+
+
+def anneal_step(states: np.ndarray, e_cur, S: int, sites, gates: np.ndarray, u,
+                temperature: float, direction: int = 1, split: int | None = None,
+                lib: ctypes.CDLL | None = None):
+    """One step of Alg. 1 for every walker: the local gate on a copy of the
+    state (``two_site_gate``), the new entanglement entropy
+    (``entanglement_entropy``), the Metropolis decision (``metropolis_accept``);
+    an accepted walker takes the new state and energy, a rejected one keeps
+    both. Returns (states, energies, accepted)."""
+    states = np.asarray(states, dtype=np.complex128)
+    prop = two_site_gate(states, S, sites, gates, lib=lib)
+    e_new = np.array([entanglement_entropy(prop[w], S, split) for w in range(prop.shape[0])])
+    acc = metropolis_accept(e_cur, e_new, u, temperature, direction)
+    out = np.where(acc[:, None], prop, states)
+    e_out = np.where(acc, e_new, np.asarray(e_cur, dtype=np.float64))
+    return out, e_out, acc

@@ -278,6 +278,55 @@ bg_status entropy_plan(bg_plan** out, int64_t walkers, int32_t spins, int32_t sp
 bg_status batched_entropy(const bg_plan* plan, const void* states, double* entropy,
                           double* eigenvalues, bg_stream_t stream);
 
+/* ---- the Metropolis decision and the whole annealing step (Alg. 1) ---------
+ * Sec. 3: after the local gate and the new entanglement entropy, each Monte
+ * Carlo procedure decides by the Metropolis algorithm ("M.A") whether to keep
+ * the new state or the current one, then repeats from the chosen state. The
+ * paper names the rule and no more; this library's reading: the energy is
+ * the entanglement entropy (or any per-walker energy the caller supplies),
+ * and a proposal moving the energy from E_cur to E_new is accepted when
+ *   delta = direction * (E_new - E_cur) <= 0,  or else when  u < exp(-delta / T),
+ * u being the walker's uniform in [0, 1) drawn by the caller, T >= 0 the
+ * temperature of the annealing schedule (T = 0 refuses every uphill move;
+ * a NaN energy is never accepted), direction = +1 to lower the energy or
+ * -1 to raise it. Computed in FP64.
+ *
+ * metropolis_select: the decision for `walkers` walkers. uniforms, e_new:
+ * DEVICE double [walkers]; e_cur: DEVICE double [walkers], set to e_new where
+ * accepted; accepted: DEVICE int32 [walkers], 1 or 0. With amplitudes > 0,
+ * the accepted walkers' proposals (DEVICE complex128, walker w at proposals
+ * + w * proposal_stride) are copied over their states (states + w *
+ * state_stride); amplitudes = 0 decides only (proposals and states may then
+ * be NULL). Temperature < 0, direction other than +-1 or a stride below
+ * `amplitudes` is BG_ERR_INVALID_ARG. Asynchronous on `stream`. */
+bg_status metropolis_select(int64_t walkers, double temperature, int32_t direction,
+                            const double* uniforms, const double* e_new, double* e_cur,
+                            int32_t* accepted, const void* proposals, int64_t proposal_stride,
+                            void* states, int64_t state_stride, int64_t amplitudes,
+                            bg_stream_t stream);
+
+/* anneal_plan / anneal_step: one whole step of Alg. 1 for `walkers` complex128
+ * states of 2^spins amplitudes (walker w at states + w * stride): each
+ * walker's proposal is its state with its local gate applied (as
+ * apply_local_gate), the proposal's entanglement entropy across the cut
+ * after the lower `split` spins is computed (as batched_entropy, the Gram
+ * matrices in `precision`), and metropolis_select keeps or replaces the
+ * state. energy: DEVICE double [walkers], the current states' entropies
+ * (from batched_entropy before the first step), updated in place; sites:
+ * DEVICE int32 [walkers]; gates: DEVICE complex128 [walkers][16] (column-major
+ * 4 x 4); uniforms: DEVICE double [walkers]; accepted: DEVICE int32 [walkers].
+ * The plan owns the entropy plan and a proposal buffer of walkers x 2^spins
+ * complex128. Argument ranges as for entropy_plan and metropolis_select;
+ * flags: 0 or BG_PLAN_PROFILE. Asynchronous; calls on one plan must not
+ * overlap. */
+bg_status anneal_plan(bg_plan** out, int64_t walkers, int32_t spins, int32_t split,
+                      int64_t stride, const bg_precision* precision, uint32_t flags,
+                      bg_stream_t stream);
+
+bg_status anneal_step(const bg_plan* plan, void* states, double* energy, const int32_t* sites,
+                      const void* gates, const double* uniforms, double temperature,
+                      int32_t direction, int32_t* accepted, bg_stream_t stream);
+
 /* ---- spreading independent work over GPUs (Sec. 4.B, Table 1) --------------
  * The paper runs its independent Monte Carlo procedures on several GPUs and
  * reports near-linear scaling (Sec. 4.B, Table 1). This host-only call splits

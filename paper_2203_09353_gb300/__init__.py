@@ -40,7 +40,8 @@ EXPORTS = ("batched_gemm_fixed", "batched_gemm_fixed_static", "batched_gemm_plan
            "bg_unitarity_drift", "bg_split_planes", "bg_check_device_errors",
            "bg_test_bounded_wait", "bg_probe_fp64_peak", "bg_launch_count", "bg_status_string",
            "bg_last_error", "bg_version", "apply_local_gate", "bg_partition_lpt",
-           "entropy_plan", "batched_entropy")
+           "entropy_plan", "batched_entropy", "metropolis_select", "anneal_plan",
+           "anneal_step")
 
 
 class BgemmError(RuntimeError):
@@ -100,6 +101,9 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "bg_partition_lpt": [i64, P(dbl), i32, P(i32), P(dbl)],
         "entropy_plan": [P(vp), i64, i32, i32, i64, P(Precision), u32, vp],
         "batched_entropy": [vp, vp, vp, vp, vp],
+        "metropolis_select": [i64, dbl, i32, vp, vp, vp, vp, vp, i64, vp, i64, i64, vp],
+        "anneal_plan": [P(vp), i64, i32, i32, i64, P(Precision), u32, vp],
+        "anneal_step": [vp, vp, vp, vp, vp, vp, dbl, i32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -336,6 +340,63 @@ def batched_entropy(plan: Plan, states, entropy, eigenvalues=None, stream=None) 
                 raise ValueError(f"batched_entropy: {name} must be contiguous")
     _check(load_library().batched_entropy(plan.handle, _ptr(states), _ptr(entropy),
                                           _ptr(eigenvalues), _stream(stream)))
+
+
+def _require(name: str, x, dtype) -> None:
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+
+
+def metropolis_select(temperature: float, direction: int, uniforms, e_new, e_cur, accepted,
+                      proposals=None, states=None, amplitudes: int = 0,
+                      proposal_stride: int | None = None, state_stride: int | None = None,
+                      walkers: int | None = None, stream=None) -> None:
+    """The Metropolis decision of Alg. 1 ("M.A") per walker; with ``amplitudes`` > 0
+    the accepted proposals are copied over the states (C ABI metropolis_select)."""
+    import torch
+    for name, x, dt in (("uniforms", uniforms, torch.float64), ("e_new", e_new, torch.float64),
+                        ("e_cur", e_cur, torch.float64), ("accepted", accepted, torch.int32),
+                        ("proposals", proposals, torch.complex128),
+                        ("states", states, torch.complex128)):
+        _require(name, x, dt)
+    if walkers is None:
+        walkers = int(e_cur.numel())
+    ps = amplitudes if proposal_stride is None else int(proposal_stride)
+    ss = amplitudes if state_stride is None else int(state_stride)
+    _check(load_library().metropolis_select(int(walkers), float(temperature), int(direction),
+                                            _ptr(uniforms), _ptr(e_new), _ptr(e_cur),
+                                            _ptr(accepted), _ptr(proposals), ps, _ptr(states), ss,
+                                            int(amplitudes), _stream(stream)))
+
+
+def anneal_plan(walkers: int, spins: int, split: int | None = None, stride: int | None = None,
+                prec: Precision | None = None, flags: int = 0, stream=None) -> Plan:
+    """Plan for whole annealing steps of Alg. 1 (C ABI anneal_plan)."""
+    split = spins // 2 if split is None else int(split)
+    stride = (1 << spins) if stride is None else int(stride)
+    h = ctypes.c_void_p()
+    _check(load_library().anneal_plan(ctypes.byref(h), int(walkers), int(spins), split, stride,
+                                      ctypes.byref(prec) if prec is not None else None,
+                                      int(flags), _stream(stream)))
+    return Plan(h.value, BG_C128, "anneal")
+
+
+def anneal_step(plan: Plan, states, energy, sites, gates, uniforms, temperature: float,
+                direction: int, accepted, stream=None) -> None:
+    """One step of Alg. 1 for every walker: local gate, entropy, Metropolis (C ABI anneal_step)."""
+    import torch
+    for name, x, dt in (("states", states, torch.complex128), ("energy", energy, torch.float64),
+                        ("sites", sites, torch.int32), ("gates", gates, torch.complex128),
+                        ("uniforms", uniforms, torch.float64),
+                        ("accepted", accepted, torch.int32)):
+        _require(name, x, dt)
+    _check(load_library().anneal_step(plan.handle, _ptr(states), _ptr(energy), _ptr(sites),
+                                      _ptr(gates), _ptr(uniforms), float(temperature),
+                                      int(direction), _ptr(accepted), _stream(stream)))
 
 
 def rel_err(dtype, d_table, A, B, C_test, C_ref, out, count: int, stream=None) -> None:

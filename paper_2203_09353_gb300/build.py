@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbgemm.so")
 
 SOURCES = ["api.cpp", "fp64.cu", "split.cu", "split_gemm_r64.cu", "split_gemm_c128.cu", "util.cu", "gate.cu",
-           "noalloc.cu", "entropy.cu"]
+           "noalloc.cu", "entropy.cu", "anneal.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]

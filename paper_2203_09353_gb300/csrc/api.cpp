@@ -218,6 +218,14 @@ struct bg_plan {
   double* d_tri_d = nullptr;
   double* d_tri_e = nullptr;
   int ent_n = 0;
+  // annealing-step plans (Alg. 1): the entropy plan over the proposals, the
+  // proposal buffer (walkers x 2^spins, contiguous) and the new energies
+  bool is_anneal = false;
+  bg_plan* ent = nullptr;
+  double2* d_prop = nullptr;
+  double* d_enew = nullptr;
+  int32_t spins = 0;
+  int64_t state_stride = 0;
   // graph cache
   cudaGraphExec_t gexec = nullptr;
   std::vector<uintptr_t> gkey;
@@ -515,6 +523,9 @@ void destroy_plan(bg_plan* p) {
   cudaFree(p->d_pool_n);
   if (p->split) split_plan_destroy(p->split);
   if (p->gram) destroy_plan(p->gram);
+  if (p->ent) destroy_plan(p->ent);
+  cudaFree(p->d_prop);
+  cudaFree(p->d_enew);
   cudaFree(p->d_gram);
   cudaFree(p->d_tri_d);
   cudaFree(p->d_tri_e);
@@ -817,7 +828,8 @@ bg_status batched_gemm_grouped(const bg_plan* plan, const void* A_base, const vo
                                bg_stream_t stream) {
   if (!plan) return fail(BG_ERR_INVALID_ARG, "plan is NULL");
   if (plan->is_chain) return fail(BG_ERR_INVALID_ARG, "chain plans run through chain_step");
-  if (plan->is_entropy) return fail(BG_ERR_INVALID_ARG, "entropy plans run through batched_entropy");
+  if (plan->is_entropy || plan->is_anneal)
+    return fail(BG_ERR_INVALID_ARG, "entropy and annealing plans have their own run calls");
   if (plan->count == 0) return BG_OK;
   if (!alpha || !beta) return fail(BG_ERR_INVALID_ARG, "alpha and beta must be host pointers");
   const Scalars sc = make_scalars(plan->dtype, alpha, beta);
@@ -1304,6 +1316,113 @@ bg_status batched_entropy(const bg_plan* plan, const void* states, double* entro
                                      entropy, eigenvalues, st);
   if (e != cudaSuccess) return cuda_fail(e, "entropy eigenvalue launch");
   if (ev) BG_CUDA(cudaEventRecord(ev[2], st), "profiling event record");
+  return BG_OK;
+}
+
+bg_status metropolis_select(int64_t walkers, double temperature, int32_t direction,
+                            const double* uniforms, const double* e_new, double* e_cur,
+                            int32_t* accepted, const void* proposals, int64_t proposal_stride,
+                            void* states, int64_t state_stride, int64_t amplitudes,
+                            bg_stream_t stream) {
+  if (walkers < 0) return fail(BG_ERR_INVALID_ARG, "negative walker count");
+  if (!(temperature >= 0.0)) return fail(BG_ERR_INVALID_ARG, "temperature must be >= 0");
+  if (direction != 1 && direction != -1) return fail(BG_ERR_INVALID_ARG, "direction must be +1 or -1");
+  if (amplitudes < 0) return fail(BG_ERR_INVALID_ARG, "negative amplitude count");
+  if (walkers == 0) return BG_OK;
+  if (!uniforms || !e_new || !e_cur || !accepted)
+    return fail(BG_ERR_INVALID_ARG, "null device pointer");
+  if (amplitudes > 0) {
+    if (!proposals || !states) return fail(BG_ERR_INVALID_ARG, "null state pointer");
+    if (proposal_stride < amplitudes || state_stride < amplitudes)
+      return fail(BG_ERR_INVALID_ARG, "strides below the amplitude count");
+    if (!aligned(proposals, BG_C128) || !aligned(states, BG_C128))
+      return fail(BG_ERR_INVALID_ARG, "states not 16-byte aligned");
+  }
+  if (fault_injected()) return fail(BG_ERR_CUDA, "injected launch failure (BGEMM_FAULT)");
+  DeviceCtx* ctx;
+  bg_status s = get_ctx(&ctx);
+  if (s != BG_OK) return s;
+  cudaError_t e = launch_metropolis(walkers, temperature, direction, uniforms, e_new, e_cur,
+                                    accepted, proposals, proposal_stride, states, state_stride,
+                                    amplitudes, ctx->sms, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "Metropolis launch");
+  return BG_OK;
+}
+
+bg_status anneal_plan(bg_plan** out, int64_t walkers, int32_t spins, int32_t split,
+                      int64_t stride, const bg_precision* precision, uint32_t flags,
+                      bg_stream_t stream) {
+  if (!out) return fail(BG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (flags & ~(uint32_t)BG_PLAN_PROFILE)
+    return fail(BG_ERR_INVALID_ARG, "annealing plans take BG_PLAN_PROFILE only");
+  bg_plan* ent = nullptr;
+  const int64_t amps = spins >= 2 && spins <= 30 ? (int64_t)1 << spins : 0;
+  // the entropy plan checks walkers, spins, split and the precision
+  bg_status s = entropy_plan(&ent, walkers, spins, split, amps, precision, flags, stream);
+  if (s != BG_OK) return s;
+  if (stride < amps) {
+    destroy_plan(ent);
+    return fail(BG_ERR_INVALID_ARG, "stride %lld below 2^spins", (long long)stride);
+  }
+  bg_plan* p = new bg_plan();
+  p->device = ent->device;
+  p->dtype = BG_C128;
+  p->prec = ent->prec;
+  p->flags = flags;
+  p->count = walkers;
+  p->is_anneal = true;
+  p->ent = ent;
+  p->spins = spins;
+  p->state_stride = stride;
+  if (walkers > 0) {
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->d_prop, (size_t)walkers * amps * sizeof(double2))) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_enew, (size_t)walkers * sizeof(double))) != cudaSuccess) {
+      destroy_plan(p);
+      return cuda_fail(e, "annealing plan workspace");
+    }
+  }
+  p->workspace_bytes = ent->workspace_bytes + walkers * (amps * (int64_t)sizeof(double2) + 8);
+  p->launches_per_call = 1 + ent->launches_per_call + 2;
+  *out = p;
+  return BG_OK;
+}
+
+bg_status anneal_step(const bg_plan* plan, void* states, double* energy, const int32_t* sites,
+                      const void* gates, const double* uniforms, double temperature,
+                      int32_t direction, int32_t* accepted, bg_stream_t stream) {
+  if (!plan) return fail(BG_ERR_INVALID_ARG, "plan is NULL");
+  if (!plan->is_anneal) return fail(BG_ERR_INVALID_ARG, "not an annealing plan");
+  if (plan->count == 0) return BG_OK;
+  if (!states || !energy || !sites || !gates || !uniforms || !accepted)
+    return fail(BG_ERR_INVALID_ARG, "null device pointer");
+  if (!aligned(states, BG_C128) || !aligned(gates, BG_C128))
+    return fail(BG_ERR_INVALID_ARG, "states or gates not 16-byte aligned");
+  if (!(temperature >= 0.0)) return fail(BG_ERR_INVALID_ARG, "temperature must be >= 0");
+  if (direction != 1 && direction != -1) return fail(BG_ERR_INVALID_ARG, "direction must be +1 or -1");
+  if (fault_injected()) return fail(BG_ERR_CUDA, "injected launch failure (BGEMM_FAULT)");
+  bg_plan* p = const_cast<bg_plan*>(plan);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t amps = (int64_t)1 << p->spins;
+  DeviceCtx* ctx;
+  bg_status s = get_ctx(&ctx);
+  if (s != BG_OK) return s;
+  // 1. the proposal: a copy of every current state ...
+  BG_CUDA(cudaMemcpy2DAsync(p->d_prop, amps * sizeof(double2), states,
+                            p->state_stride * sizeof(double2), amps * sizeof(double2), p->count,
+                            cudaMemcpyDeviceToDevice, st),
+          "proposal copy");
+  // 2. ... with the walker's local gate applied ("Apply Local Gate")
+  cudaError_t e = launch_local_gate(p->count, p->spins, sites, gates, p->d_prop, amps, ctx->d_err,
+                                    ctx->sms, st);
+  if (e != cudaSuccess) return cuda_fail(e, "local gate launch");
+  // 3. its entanglement entropy ("Calculate Entropy")
+  if ((s = batched_entropy(p->ent, p->d_prop, p->d_enew, nullptr, stream)) != BG_OK) return s;
+  // 4. the Metropolis decision ("M.A"): accepted proposals replace the states
+  e = launch_metropolis(p->count, temperature, direction, uniforms, p->d_enew, energy, accepted,
+                        p->d_prop, amps, states, p->state_stride, amps, ctx->sms, st);
+  if (e != cudaSuccess) return cuda_fail(e, "Metropolis launch");
   return BG_OK;
 }
 

@@ -122,4 +122,11 @@ bg_status static_scratch(void** out, size_t* bytes, std::string* err);
 cudaError_t launch_entropy_eig(double2* gram, int64_t walkers, int n, double* d, double* e,
                                double* entropy, double* eigs, cudaStream_t st);
 
+// Metropolis decision per walker and copy of the accepted proposals over the
+// current states (anneal.cu). prop / cur may be null when amps == 0.
+cudaError_t launch_metropolis(int64_t walkers, double T, int direction, const double* u,
+                              const double* e_new, double* e_cur, int32_t* acc,
+                              const void* prop, int64_t pstride, void* cur, int64_t cstride,
+                              int64_t amps, int sms, cudaStream_t st);
+
 }  // namespace bg

@@ -69,7 +69,8 @@ def parse_args():
     p.add_argument("--count", type=int, default=20000, help="instances (the size mixes)")
     p.add_argument("--mode", default="split9", help="headline mode: fp64 or splitS")
     p.add_argument("--modes", default="fp64,split3,split6,split9")
-    p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--fp64-steps", type=int, default=0,
+                   help="timed steps of the FP64 mode (0: as --steps)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-chunks", type=int, default=4, help="instance ranges of the e2e pipeline")
@@ -81,6 +82,14 @@ def parse_args():
                    help="skip the Hermitian-update line (rho = Psi Psi^H, Sec. 3 shapes)")
     p.add_argument("--no-chain", action="store_true",
                    help="skip the chained-product line (1024 walkers, Alg. 1 step loop)")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the fixed-size and uniform-mix workloads (configs 1-3)")
+    p.add_argument("--no-entropy", action="store_true",
+                   help="skip the entanglement-entropy line (128 states of 17 spins)")
+    p.add_argument("--no-anneal", action="store_true",
+                   help="skip the whole-annealing-step line (gate, entropy, Metropolis)")
+    p.add_argument("--no-ablation", action="store_true",
+                   help="skip the tasked-vs-batched ablation (N streams of plans vs one launch)")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
 
@@ -526,8 +535,279 @@ def chain_line(bg, fp64_steps: int = 10, split_steps: int = 200):
         res[mode] = {"steps": steps, "ms": ms, "ms_per_step": ms / steps,
                      "value": step_flops * steps / (ms * 1e-3) / 1e12, "unit": UNIT,
                      "max_unitarity_drift": float(drift.max())}
+        if steps < split_steps:
+            # a bounded number of the 200 steps, timed; the whole run extrapolated linearly
+            res[mode]["extrapolated"] = {"steps": split_steps, "ms": ms / steps * split_steps,
+                                         "from_timed_steps": steps}
         plan.close()
     return res
+
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _time_calls(fn, steps: int, warmup: int, flush=None) -> float:
+    """Mean device ms of fn() over `steps` calls after `warmup`, CUDA events on the
+    current stream. With `flush`, each call is timed alone and flush() (a write
+    larger than L2) runs between calls outside the timed pairs."""
+    import torch
+    for _ in range(max(1, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    if flush is None:
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+    total = 0.0
+    for _ in range(steps):
+        flush()
+        e0, e1 = _events()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps
+
+
+def configs_line(bg, pk, fp64_peak, steps: int, warmup: int, cpu_seconds: float, cache: str):
+    """The three workloads besides the log-uniform headline mix: 64 real n = 32
+    instances, 4096 complex n = 64 Hermitian x Haar-unitary instances, and the
+    20000-instance U[-1,1] size mix (alpha = 1, beta = 0.5) -- the last as one
+    autotuned persistent launch replayed from a captured CUDA graph, with a
+    per-size-class FP64 rate. Each in FP64 and with 9 slices; the roofline of
+    the FP64 path is min(FP64 peak, intensity x copy bandwidth)."""
+    import torch
+    from paper_2203_09353_gb300 import synth
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, make in (("fixed-n32", synth.fixed_real_n32), ("complex-n64",
+                       synth.hermitian_unitary_c128), ("mix-uniform", synth.size_mix_uniform)):
+        b = make()
+        flops, nbytes = b.flops(), b.bytes_moved()
+        inten = flops / nbytes
+        roof = min(fp64_peak, inten * pk["hbm_gbs"] / 1e3)
+        A, B, C0 = (torch.from_numpy(x).cuda() for x in (b.A, b.B, b.C))
+        dtab = torch.from_numpy(b.table).cuda()
+        small = nbytes < 64e6  # inputs smaller than L2: flush between timed calls
+        res = {"workload": b.name, "instances": b.count, "gflop": flops / 1e9,
+               "algorithmic_gb": nbytes / 1e9, "intensity_flop_per_byte": inten,
+               "l2": "flushed (256 MB write) between timed calls" if small else
+                     "inputs larger than L2, no flush"}
+        outs = {}
+        for mode in ("fp64", "split9"):
+            prec = None if mode == "fp64" else bg.precision("split", 9)
+            flags = bg.BG_PLAN_CAPTURE_GRAPH | (bg.BG_PLAN_AUTOTUNE | bg.BG_PLAN_USE_CACHE
+                                                if mode == "fp64" else 0)
+            plan = bg.batched_gemm_plan(b.dtype, b.table, prec, flags, cache)
+            C = C0.clone()
+            call = lambda: bg.batched_gemm_grouped(plan, A, B, C, b.alpha, b.beta)
+            ms = _time_calls(call, steps, warmup, (lambda: flush_buf.zero_()) if small else None)
+            C.copy_(C0)
+            call()
+            torch.cuda.synchronize()
+            outs[mode] = C
+            tf = flops / (ms * 1e-3) / 1e12
+            res[mode] = {"ms_per_call": ms, "value": tf, "unit": UNIT,
+                         "frac_of_fp64_roofline": tf / roof,
+                         "graph": True, "autotuned": mode == "fp64"}
+            if mode == "fp64":
+                res["fp64_roofline"] = {"bound": "alu" if fp64_peak <= inten * pk["hbm_gbs"] / 1e3
+                                        else "hbm", "peak": roof, "unit": "TFLOP/s",
+                                        "fp64_peak": fp64_peak, "hbm_gbs": pk["hbm_gbs"]}
+                res["plan"] = json.loads(plan.describe())
+            plan.close()
+        errbuf = torch.zeros(b.count, dtype=torch.float64, device="cuda")
+        bg.rel_err(b.dtype, dtab, A, B, outs["split9"], outs["fp64"], errbuf, b.count)
+        res["split9"]["max_err_vs_fp64_path_all"] = float(errbuf.max())
+        ids = calibrated_sample(b, cpu_seconds) if b.count > 64 else np.arange(b.count)
+        ref, dt, fl, threads = oracle_on(b, ids)
+        for mode in ("fp64", "split9"):
+            res[mode]["max_err_vs_oracle"] = sample_errors(b, outs[mode].cpu().numpy(), ref)
+        res["oracle_sample"] = f"{len(ids)} of {b.count} instances, {threads} cores, {dt:.2f} s"
+        if name == "mix-uniform":
+            # FP64 rate per size class: one autotuned plan over the class's instances
+            per = {}
+            for n in synth.SIZE_MIX_SIZES:
+                sel = np.flatnonzero(b.table[:, 0] == n)
+                if sel.size == 0:
+                    continue
+                sub = b.table[sel]
+                plan = bg.batched_gemm_plan("r64", sub, None, bg.BG_PLAN_AUTOTUNE |
+                                            bg.BG_PLAN_USE_CACHE | bg.BG_PLAN_CAPTURE_GRAPH, cache)
+                C = C0.clone()
+                ms = _time_calls(lambda: bg.batched_gemm_grouped(plan, A, B, C, b.alpha, b.beta),
+                                 steps, warmup)
+                fl = float(np.sum(2.0 * sub[:, 0] * sub[:, 1] * sub[:, 2]))
+                tf = fl / (ms * 1e-3) / 1e12
+                per[str(n)] = {"instances": int(sel.size), "ms": ms, "value": tf,
+                               "frac_of_fp64_peak": tf / fp64_peak,
+                               "program": json.loads(plan.describe())["classes"][0]["program"]}
+                plan.close()
+            res["fp64_per_class"] = per
+        out[name] = res
+        del A, B, C0, outs
+    return out
+
+
+def entropy_line(bg, fp64_peak, steps: int = 5, warmup: int = 2, S: int = 17,
+                 walkers: int = 128):
+    """The entanglement entropy of Alg. 1 ("Calculate Entropy") for `walkers`
+    random complex states of S spins (cut after floor(S/2) spins: K = 256,
+    M = 512 at S = 17): the Gram matrices through the Hermitian update (FP64 or
+    9 slices), then FP64 tridiagonalisation and bisection. Roofline of the
+    eigenvalue step: FP64 flops of the reduction, (16/3) K^3 per walker (the
+    LAPACK count of zhetrd), against the live DFMA probe."""
+    import torch
+    import oracle
+    K = 1 << (S // 2)
+    gen = torch.Generator(device="cuda").manual_seed(31)
+    psi = torch.randn(walkers << S, dtype=torch.complex128, device="cuda", generator=gen)
+    ent = torch.zeros(walkers, dtype=torch.float64, device="cuda")
+    sample = list(range(0, walkers, max(1, walkers // 4)))[:4]
+    host_psi = psi.view(walkers, 1 << S)[sample].cpu().numpy()
+    t0 = time.perf_counter()
+    want = np.array([oracle.entanglement_entropy(p, S) for p in host_psi])
+    cpu_s = (time.perf_counter() - t0) / len(sample)
+    res = {"workload": f"{walkers} complex states of {S} spins, cut after {S // 2} spins "
+                       f"(Gram matrices {K} x {K} from {K} x {1 << (S - S // 2)} views)",
+           "cpu_oracle_s_per_walker": cpu_s}
+    tri_flops = walkers * 16.0 / 3.0 * K ** 3
+    for mode in ("fp64", "split9"):
+        prec = None if mode == "fp64" else bg.precision("split", 9)
+        plan = bg.entropy_plan(walkers, S, prec=prec, flags=bg.BG_PLAN_PROFILE)
+        for _ in range(warmup):
+            bg.batched_entropy(plan, psi, ent)
+        plan.kernel_times(reset=True)
+        ms = _time_calls(lambda: bg.batched_entropy(plan, psi, ent), steps, 0)
+        kt, calls = plan.kernel_times(reset=True)
+        got = ent.cpu().numpy()[sample]
+        eig_ms = kt[1] / max(calls, 1)
+        ach = tri_flops / (eig_ms * 1e-3) / 1e12
+        res[mode] = {"ms_per_call": ms, "gram_ms": kt[0] / max(calls, 1), "eig_ms": eig_ms,
+                     "value": walkers / (ms * 1e-3), "unit": "walkers/s",
+                     "max_abs_err_vs_oracle": float(np.max(np.abs(got - want))),
+                     "eig_roofline": {"kernels": "tridiag_kernel + bisect_kernel", "bound": "alu",
+                                      "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                                      "frac": ach / fp64_peak,
+                                      "flops": "(16/3) K^3 per walker (Householder reduction)"}}
+        plan.close()
+    return res
+
+
+def anneal_line(bg, steps: int = 10, warmup: int = 2, S: int = 17, walkers: int = 128):
+    """Whole annealing steps of Alg. 1 for `walkers` states of S spins: per step
+    and walker a Haar gate on a random neighbouring pair, the proposal's
+    entropy (Gram with 9 slices, FP64 eigenvalues) and the Metropolis decision
+    at a geometric temperature schedule T_t = 0.05 x 0.9^t, minimising the
+    entropy. The CPU oracle's step is timed on two walkers for context."""
+    import torch
+    import oracle
+    rng = np.random.default_rng(37)
+    gen = torch.Generator(device="cuda").manual_seed(37)
+    dim = 1 << S
+    psi = torch.randn(walkers * dim, dtype=torch.complex128, device="cuda", generator=gen)
+    psi /= psi.view(walkers, dim).abs().pow(2).sum(dim=1).sqrt().repeat_interleave(dim)
+    prec = bg.precision("split", 9)
+    eplan = bg.entropy_plan(walkers, S, prec=prec)
+    energy = torch.zeros(walkers, dtype=torch.float64, device="cuda")
+    bg.batched_entropy(eplan, psi, energy)
+    e_start = float(energy.mean())
+    total = warmup + steps
+    z = rng.standard_normal((total, walkers, 4, 4)) + 1j * rng.standard_normal((total, walkers, 4, 4))
+    q, r = np.linalg.qr(z)
+    d = np.diagonal(r, axis1=-2, axis2=-1)
+    haar = q * (d / np.abs(d))[..., None, :]
+    gates = torch.from_numpy(np.ascontiguousarray(haar.transpose(0, 1, 3, 2))).cuda()
+    sites_h = rng.integers(0, S - 1, (total, walkers)).astype(np.int32)
+    sites = torch.from_numpy(sites_h).cuda()
+    u_h = rng.random((total, walkers))
+    u = torch.from_numpy(u_h).cuda()
+    acc = torch.zeros(walkers, dtype=torch.int32, device="cuda")
+    plan = bg.anneal_plan(walkers, S, prec=prec)
+    temps = [0.05 * 0.9 ** t for t in range(total)]
+    host0 = psi.view(walkers, dim)[:2].cpu().numpy()
+    e0_host = energy[:2].cpu().numpy()
+    for t in range(warmup):
+        bg.anneal_step(plan, psi, energy, sites[t], gates[t], u[t], temps[t], 1, acc)
+    torch.cuda.synchronize()
+    accepted = 0
+    e0, e1 = _events()
+    e0.record()
+    for t in range(warmup, total):
+        bg.anneal_step(plan, psi, energy, sites[t], gates[t], u[t], temps[t], 1, acc)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    accepted = int(acc.sum())  # last step's acceptances
+    t0 = time.perf_counter()
+    oracle.anneal_step(host0, e0_host, S, sites_h[0, :2], haar[0, :2], u_h[0, :2], temps[0], 1)
+    cpu_step = (time.perf_counter() - t0) / 2
+    return {"workload": f"{walkers} complex states of {S} spins; gate on a random pair, "
+                        f"entropy across the middle cut (Gram with 9 slices), Metropolis "
+                        f"minimising it at T_t = 0.05 x 0.9^t",
+            "steps": steps, "ms_per_step": ms, "value": walkers / (ms * 1e-3),
+            "unit": "walker-steps/s", "mean_entropy_start": e_start,
+            "mean_entropy_end": float(energy.mean()),
+            "accepted_last_step": accepted,
+            "cpu_oracle": {"s_per_walker_step": cpu_step, "walker_steps": 2,
+                           "note": "the oracle's gate, entropy (numpy eigvalsh) and decision"}}
+
+
+def ablation_line(bg, batch, A, B, C0, steps: int, warmup: int, streams=(1, 4, 8, 16)):
+    """The paper's taskedGEMM against its batchedGEMM, with this library's kernels
+    (Sec. 3, Sec. 4.A): per size class of the log-uniform mix, N concurrent
+    streams each submitting its own round-robin share of the class's instances
+    as one grouped call (the tasks), against N = 1 (one launch for the whole
+    class), and the whole mix as one launch against 16 tasks. FP64 and 9
+    slices, default tile programs in both arms."""
+    import torch
+    cur = torch.cuda.current_stream()
+    pool = [torch.cuda.Stream() for _ in range(max(streams))]
+    out = {}
+    classes = [(str(n), np.flatnonzero(batch.table[:, 0] == n)) for n in
+               sorted(set(int(x) for x in batch.table[:, 0]))]
+    classes.append(("all", np.arange(batch.count)))
+    for mode in ("fp64", "split9"):
+        prec = None if mode == "fp64" else bg.precision("split", 9)
+        res = {}
+        for cname, sel in classes:
+            row = {}
+            fl = float(np.sum(2.0 * batch.table[sel, 0] * batch.table[sel, 1] *
+                              batch.table[sel, 2]))
+            for N in (streams if cname != "all" else (1, max(streams))):
+                parts = [sel[j::N] for j in range(N) if sel[j::N].size]
+                plans = [bg.batched_gemm_plan("r64", batch.table[p], prec) for p in parts]
+                C = C0.clone()
+
+                def tasks():
+                    for s in pool[:len(plans)]:
+                        s.wait_stream(cur)
+                    for s, pl in zip(pool, plans):
+                        with torch.cuda.stream(s):
+                            bg.batched_gemm_grouped(pl, A, B, C, batch.alpha, batch.beta,
+                                                    stream=s)
+                    for s in pool[:len(plans)]:
+                        cur.wait_stream(s)
+
+                ms = _time_calls(tasks, steps, warmup)
+                row[f"N={N}"] = {"ms": ms, "value": fl / (ms * 1e-3) / 1e12}
+                for pl in plans:
+                    pl.close()
+                del C
+            row["batched_over_tasked16"] = (row[f"N={max(streams)}"]["ms"] /
+                                            row["N=1"]["ms"])
+            res[cname] = row
+        out[mode] = res
+    out["unit"] = UNIT
+    return out
+
 
 
 def run_reference(args, world, rank, pg):
@@ -648,7 +928,7 @@ def main():
     clocks = None
     launches = 0
     for m in modes:
-        steps = args.fp64_steps if m == "fp64" and m != args.mode else args.steps
+        steps = (args.fp64_steps or args.steps) if m == "fp64" and m != args.mode else args.steps
         Cm = C0.clone()
         for _ in range(args.warmup):
             bg.batched_gemm_grouped(plans[m], A, B, Cm, batch.alpha, batch.beta)
@@ -825,6 +1105,27 @@ def main():
         herk = herk_line(bg, steps=max(2, args.steps // 2), warmup=1)
         log(f"Hermitian update: {json.dumps(herk)}")
 
+    ablation = None
+    if not args.no_ablation and batch.dtype == "r64" and args.workload.startswith("mix-"):
+        ablation = ablation_line(bg, batch, A, B, C0, steps=3, warmup=1)
+        log(f"ablation: {json.dumps(ablation)}")
+
+    configs = None
+    if not args.no_configs:
+        configs = configs_line(bg, pk, fp64_peak, steps=max(3, args.steps // 2), warmup=2,
+                               cpu_seconds=min(args.cpu_seconds, 4.0), cache=cache)
+        log(f"configs: {json.dumps(configs)}")
+
+    entropy = None
+    if not args.no_entropy:
+        entropy = entropy_line(bg, fp64_peak)
+        log(f"entropy: {json.dumps(entropy)}")
+
+    anneal = None
+    if not args.no_anneal:
+        anneal = anneal_line(bg)
+        log(f"anneal: {json.dumps(anneal)}")
+
     if rank != 0:
         return
     h = res[head]
@@ -855,6 +1156,10 @@ def main():
         "herk": herk,
         "chain": chain,
         "gate": gate,
+        "configs": configs,
+        "entropy": entropy,
+        "anneal": anneal,
+        "ablation": ablation,
         "peaks_source": pk_src,
     }
     print(json.dumps(line), flush=True)

@@ -259,7 +259,7 @@ bg_status apply_local_gate(bg_dtype dtype, int64_t walkers, int32_t spins, const
  *    eigenvalues of rho_w = Psi Psi^H. p_i = lambda_i(G_w) / sum_j lambda_j.
  *  - entropy_plan: `walkers` complex128 states of 2^spins amplitudes, walker w
  *    at element w * stride (stride >= 2^spins); 2 <= spins <= 30,
- *    1 <= split <= min(spins - 1, 11). precision (NULL = FP64) selects the
+ *    1 <= split <= min(spins - 1, 10). precision (NULL = FP64) selects the
  *    precision of G_w: it is formed by a Hermitian-update plan
  *    (BG_PLAN_HERK) in that mode. The eigenvalues are always computed in
  *    FP64: Householder reduction of G_w to a real tridiagonal matrix, then

@@ -1240,8 +1240,8 @@ bg_status entropy_plan(bg_plan** out, int64_t walkers, int32_t spins, int32_t sp
   if (walkers < 0 || walkers > 65535)
     return fail(BG_ERR_INVALID_ARG, "walkers = %lld outside 0..65535", (long long)walkers);
   if (spins < 2 || spins > 30) return fail(BG_ERR_INVALID_ARG, "spins = %d outside 2..30", spins);
-  if (split < 1 || split > spins - 1 || split > 11)
-    return fail(BG_ERR_INVALID_ARG, "split = %d outside 1..min(spins - 1, 11)", split);
+  if (split < 1 || split > spins - 1 || split > 10)
+    return fail(BG_ERR_INVALID_ARG, "split = %d outside 1..min(spins - 1, 10)", split);
   if (stride < ((int64_t)1 << spins))
     return fail(BG_ERR_INVALID_ARG, "stride %lld below 2^spins", (long long)stride);
   if (flags & ~(uint32_t)BG_PLAN_PROFILE)

@@ -12,8 +12,8 @@
 //    lower triangle: for column j, the reflector H = I - tau v v^H that maps
 //    G[j+1:, j] to (beta, 0, ..., 0) (beta real), then
 //    G22 <- G22 - v w^H - w v^H with p = tau G22 v, w = p - (tau/2)(p^H v) v.
-//    The matrix is first mirrored to both triangles so that the Hermitian
-//    product and the rank-2 update read and write whole columns (coalesced).
+//    Only the lower triangle is touched: a warp per column of the trailing
+//    matrix, its lanes down the column (coalesced).
 //  * bisect_kernel: every eigenvalue of the tridiagonal matrix by bisection
 //    on the Sturm count (the number of negative pivots of T - x I), one thread
 //    per eigenvalue, then the entropy by a block reduction.
@@ -29,16 +29,17 @@
 namespace bg {
 namespace {
 
-constexpr int kEntThreads = 256;
+constexpr int kEntThreads = 256;      // bisection; reduction for n > 512
+constexpr int kEntMaxThreads = 512;   // reduction for n <= 512
 
 struct Z {
   double re, im;
 };
 __device__ __forceinline__ Z zmul(Z a, Z b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-__device__ __forceinline__ Z zconj(Z a) { return {a.re, -a.im}; }
 __device__ __forceinline__ Z zadd(Z a, Z b) { return {a.re + b.re, a.im + b.im}; }
 
 // Sum of v over the block (all threads call it; the result reaches every thread).
+// red: one double per warp.
 __device__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -61,44 +62,58 @@ __device__ double block_max(double v, double* red) {
   return s;
 }
 
+// acc + a b and acc + conj(a) b as four FP64 fused multiply-adds each
+__device__ __forceinline__ Z zfma(Z a, Z b, Z acc) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+__device__ __forceinline__ Z zfma_conj(Z a, Z b, Z acc) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+
+
 // Householder tridiagonalisation of the n x n Hermitian matrices G_w (lower
-// triangle given; column-major, leading dimension n, walker w at G + w n n).
-// Writes d[w n + i] (diagonal) and e[w n + i] (sub-diagonal, i < n - 1). G is
-// overwritten. Dynamic shared memory: v and w, 2 n complex.
-__global__ void __launch_bounds__(kEntThreads) tridiag_kernel(double2* G, int n, double* d,
-                                                              double* e) {
+// triangle, column-major, leading dimension n, walker w at G + w n n; only the
+// lower triangle is read or written). Writes d[w n + i] (diagonal) and
+// e[w n + i] (sub-diagonal, i < n - 1). Each warp takes whole columns of the
+// trailing matrix (its lanes run down the column, coalesced): the Hermitian
+// product p = G22 v from the lower triangle alone adds G22[i, c] v[c] into
+// the warp's own partial vector for rows i >= c and conj(G22[i, c]) v[i]
+// into the column's dot product for row c; the rank-2 update then rewrites
+// the lower triangle. Dynamic shared memory: v, w and the warps' partial
+// products, (2 + WARPS) n complex.
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) tridiag_kernel(double2* G, int n, double* d,
+                                                             double* e) {
+  constexpr int kEntWarps = WARPS;
   extern __shared__ double2 sm[];
   Z* v = reinterpret_cast<Z*>(sm);
   Z* w = v + n;
-  __shared__ double red[kEntThreads / 32];
+  Z* part = w + n;  // kEntWarps x n
+  __shared__ double red[kEntWarps];
   __shared__ double s_beta, s_tau_re, s_tau_im, s_sc_re, s_sc_im;
   __shared__ int s_skip;
   double2* A = G + (size_t)blockIdx.x * n * n;
   double* dw = d + (size_t)blockIdx.x * n;
   double* ew = e + (size_t)blockIdx.x * n;
-  const int t = threadIdx.x, T = blockDim.x;
+  const int t = threadIdx.x, T = blockDim.x, warp = t >> 5, lane = t & 31;
   auto at = [&](int r, int c) -> double2& { return A[r + (size_t)c * n]; };
-
-  // mirror the lower triangle into the upper one; real diagonal
-  for (int c = 0; c < n; ++c)
-    for (int r = c + t; r < n; r += T) {
-      double2 x = at(r, c);
-      if (r == c) {
-        x.y = 0.0;
-        at(r, c) = x;
-      } else {
-        at(c, r) = make_double2(x.x, -x.y);
-      }
-    }
-  __syncthreads();
 
   for (int j = 0; j < n - 1; ++j) {
     const int m = n - j - 1;  // order of the trailing matrix G22 = A[j+1:, j+1:]
+    double2* A22 = A + (j + 1) + (size_t)(j + 1) * n;
     // ---- reflector of the column below the diagonal (zlarfg)
     double xn2 = 0.0;
     for (int i = 1 + t; i < m; i += T) {
       const double2 x = at(j + 1 + i, j);
-      xn2 += x.x * x.x + x.y * x.y;
+      xn2 = fma(x.x, x.x, fma(x.y, x.y, xn2));
     }
     xn2 = block_sum(xn2, red);
     if (t == 0) {
@@ -124,43 +139,63 @@ __global__ void __launch_bounds__(kEntThreads) tridiag_kernel(double2* G, int n,
     if (s_skip) continue;
     const Z tau = {s_tau_re, s_tau_im}, sc = {s_sc_re, s_sc_im};
     for (int i = t; i < m; i += T) {
-      Z vi;
-      if (i == 0) {
-        vi = {1.0, 0.0};
-      } else {
+      Z vi = {1.0, 0.0};
+      if (i > 0) {
         const double2 x = at(j + 1 + i, j);
         vi = zmul({x.x, x.y}, sc);
       }
       v[i] = vi;
     }
+    for (int i = t; i < kEntWarps * m; i += T) part[i] = {0.0, 0.0};
     __syncthreads();
-    // ---- p = tau G22 v (rows of this thread), then alpha2 = -tau/2 (p^H v)
-    double pr = 0.0, pi_ = 0.0;  // p^H v, partial
+    // ---- partial products of p = G22 v from the lower triangle, a warp per column
+    Z* pw = part + warp * m;
+    for (int c = warp; c < m; c += kEntWarps) {
+      const double2* col = A22 + (size_t)c * n;
+      const Z vc = v[c];
+      Z dot = {0.0, 0.0};
+      for (int i = c + lane; i < m; i += 32) {
+        const double2 a2 = col[i];
+        const Z a = {a2.x, a2.y};
+        pw[i] = zfma(a, vc, pw[i]);                // G22[i, c] v[c], row i
+        if (i > c) dot = zfma_conj(a, v[i], dot);  // conj(G22[i, c]) v[i], row c
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        dot.re += __shfl_xor_sync(0xFFFFFFFFu, dot.re, o);
+        dot.im += __shfl_xor_sync(0xFFFFFFFFu, dot.im, o);
+      }
+      __syncwarp();
+      if (lane == 0) pw[c] = zadd(pw[c], dot);
+      __syncwarp();
+    }
+    __syncthreads();
+    // ---- p = tau sum of the partials, alpha2 = -tau/2 (p^H v), w = p + alpha2 v
+    double pr = 0.0, pi_ = 0.0;
     for (int i = t; i < m; i += T) {
       Z acc = {0.0, 0.0};
-      for (int c = 0; c < m; ++c) {
-        const double2 a = at(j + 1 + i, j + 1 + c);
-        acc = zadd(acc, zmul({a.x, a.y}, v[c]));
-      }
+#pragma unroll
+      for (int q = 0; q < kEntWarps; ++q) acc = zadd(acc, part[q * m + i]);
       const Z p = zmul(tau, acc);
       w[i] = p;
-      const Z pv = zmul(zconj(p), v[i]);
+      const Z pv = zfma_conj(p, v[i], {0.0, 0.0});
       pr += pv.re;
       pi_ += pv.im;
     }
     pr = block_sum(pr, red);
     pi_ = block_sum(pi_, red);
     const Z alpha2 = zmul({-0.5 * tau.re, -0.5 * tau.im}, {pr, pi_});
-    for (int i = t; i < m; i += T) w[i] = zadd(w[i], zmul(alpha2, v[i]));
+    for (int i = t; i < m; i += T) w[i] = zfma(alpha2, v[i], w[i]);
     __syncthreads();
-    // ---- G22 <- G22 - v w^H - w v^H (whole columns, both triangles)
-    for (int c = 0; c < m; ++c) {
-      const Z wc = zconj(w[c]), vc = zconj(v[c]);
-      for (int i = t; i < m; i += T) {
-        double2& a = at(j + 1 + i, j + 1 + c);
-        const Z u = zadd(zmul(v[i], wc), zmul(w[i], vc));
-        a.x -= u.re;
-        a.y -= u.im;
+    // ---- G22 <- G22 - v w^H - w v^H on the lower triangle, a warp per column
+    for (int c = warp; c < m; c += kEntWarps) {
+      double2* col = A22 + (size_t)c * n;
+      const Z wc = {-w[c].re, w[c].im}, vc = {-v[c].re, v[c].im};  // -conj(w[c]), -conj(v[c])
+      for (int i = c + lane; i < m; i += 32) {
+        Z a = {col[i].x, col[i].y};
+        a = zfma(v[i], wc, a);
+        a = zfma(w[i], vc, a);
+        col[i] = make_double2(a.re, a.im);
       }
     }
     __syncthreads();
@@ -189,7 +224,7 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* e2, in
 
 // Eigenvalues of each walker's tridiagonal matrix by bisection, then
 // S = -sum p ln p with p = lambda / sum(lambda) over p > 0. Dynamic shared
-// memory: d, e^2 and the eigenvalues, 3 n doubles.
+// memory: d, e^2 and the eigenvalues, 3 n doubles, then T + 1 int counts.
 __global__ void __launch_bounds__(kEntThreads) bisect_kernel(const double* d, const double* e,
                                                              int n, double* entropy,
                                                              double* eigs) {
@@ -221,9 +256,24 @@ __global__ void __launch_bounds__(kEntThreads) bisect_kernel(const double* d, co
   lo -= tol;
   hi += tol;
   __syncthreads();
+  // multisection: one Sturm count per thread on an even grid of [lo, hi]
+  // gives every eigenvalue a bracket T times narrower to start from
+  int* cnt = reinterpret_cast<int*>(lam + n);  // T + 1 counts
+  const double hstep = (hi - lo) / T;
+  cnt[t + 1] = t + 1 < T ? sturm_count(sd, se2, n, lo + (t + 1) * hstep, pivmin) : n;
+  if (t == 0) cnt[0] = 0;
+  __syncthreads();
   for (int k = t; k < n; k += T) {
     // the k-th smallest eigenvalue: count(a) <= k < count(b)
-    double a = lo, b = hi;
+    int g = 0;  // last grid point with count <= k (counts are nondecreasing)
+    int lo_i = 0, hi_i = T;
+    while (hi_i - lo_i > 1) {
+      const int mid = (lo_i + hi_i) >> 1;
+      if (cnt[mid] <= k) lo_i = mid;
+      else hi_i = mid;
+    }
+    g = lo_i;
+    double a = lo + g * hstep, b = g + 1 < T ? lo + (g + 1) * hstep : hi;
     for (int it = 0; it < 200 && b - a > tol; ++it) {
       const double mid = 0.5 * (a + b);
       if (sturm_count(sd, se2, n, mid, pivmin) <= k) a = mid;
@@ -250,15 +300,22 @@ __global__ void __launch_bounds__(kEntThreads) bisect_kernel(const double* d, co
 cudaError_t launch_entropy_eig(double2* gram, int64_t walkers, int n, double* d, double* e,
                                double* entropy, double* eigs, cudaStream_t st) {
   if (walkers <= 0) return cudaSuccess;
-  const size_t sm1 = 2 * (size_t)n * sizeof(double2);
-  const size_t sm2 = 3 * (size_t)n * sizeof(double);
+  const int warps = n <= 512 ? kEntMaxThreads / 32 : kEntThreads / 32;
+  const size_t sm1 = (2 + (size_t)warps) * n * sizeof(double2);
+  const size_t sm2 = 3 * (size_t)n * sizeof(double) + (kEntThreads + 1) * sizeof(int);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(tridiag_kernel<kEntMaxThreads / 32>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tridiag_kernel<kEntThreads / 32>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     attr = true;
   }
-  tridiag_kernel<<<(unsigned)walkers, kEntThreads, sm1, st>>>(gram, n, d, e);
+  if (warps == kEntMaxThreads / 32)
+    tridiag_kernel<kEntMaxThreads / 32><<<(unsigned)walkers, kEntMaxThreads, sm1, st>>>(gram, n, d, e);
+  else
+    tridiag_kernel<kEntThreads / 32><<<(unsigned)walkers, kEntThreads, sm1, st>>>(gram, n, d, e);
   count_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;

@@ -1029,29 +1029,66 @@ def main():
             chunks.append((bg.batched_gemm_plan(batch.dtype, batch.table[i0:i1], prec_h, flags_h,
                                                 cache), rng))
         s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+        # two device buffer sets, alternating between steps, so that the copies of
+        # step k + 1 need not wait for the GEMMs of step k
+        sets = [(A, B, Cd), (torch.empty_like(A), torch.empty_like(B), torch.empty_like(Cd))]
+        free_ev = [None, None]  # set k: its last GEMM and read-back of two steps ago
+        stepc = [0]
 
         def e2e_step():
+            Ad, Bd, Cdd = sets[stepc[0] & 1]
             done_in, done_gemm = [], []
-            s_in.wait_stream(stream)
+            if free_ev[stepc[0] & 1] is not None:
+                s_in.wait_event(free_ev[stepc[0] & 1])
             for _, ((a0, a1), (b0, b1), (c0, c1)) in chunks:
                 with torch.cuda.stream(s_in):
-                    A[a0:a1].copy_(Ah[a0:a1], non_blocking=True)
-                    B[b0:b1].copy_(Bh[b0:b1], non_blocking=True)
-                    Cd[c0:c1].copy_(Ch[c0:c1], non_blocking=True)
+                    Ad[a0:a1].copy_(Ah[a0:a1], non_blocking=True)
+                    Bd[b0:b1].copy_(Bh[b0:b1], non_blocking=True)
+                    Cdd[c0:c1].copy_(Ch[c0:c1], non_blocking=True)
                     ev = torch.cuda.Event()
                     ev.record(s_in)
                     done_in.append(ev)
             for (plan_j, _), ev in zip(chunks, done_in):
                 stream.wait_event(ev)
-                bg.batched_gemm_grouped(plan_j, A, B, Cd, batch.alpha, batch.beta, stream=stream)
+                bg.batched_gemm_grouped(plan_j, Ad, Bd, Cdd, batch.alpha, batch.beta, stream=stream)
                 evg = torch.cuda.Event()
                 evg.record(stream)
                 done_gemm.append(evg)
             for (_, (_, _, (c0, c1))), evg in zip(chunks, done_gemm):
                 s_out.wait_event(evg)
                 with torch.cuda.stream(s_out):
-                    Co[c0:c1].copy_(Cd[c0:c1], non_blocking=True)
+                    Co[c0:c1].copy_(Cdd[c0:c1], non_blocking=True)
+            fe = torch.cuda.Event()
+            fe.record(s_out)  # after the last read-back, which follows the last GEMM
+            free_ev[stepc[0] & 1] = fe
+            stepc[0] += 1
+
+        def timed_steps(n):
+            for s in (s_in, s_out):
+                s.wait_stream(stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for s in (s_in, s_out):
+                s.wait_stream(stream)
+            for _ in range(n):
+                e2e_step()
+            stream.wait_stream(s_in)
             stream.wait_stream(s_out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / n
+
+        def timed_alone(fn, n=3):
+            """One resource of the pipeline alone, on the current stream."""
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(n):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / n
 
         for _ in range(max(1, args.warmup)):
             e2e_step()
@@ -1063,17 +1100,26 @@ def main():
             "pipelined end-to-end result differs from the whole-batch call"
         barrier(pg)
         n2 = max(2, args.steps // 2)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(n2):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = max_over_ranks(pg, e0.elapsed_time(e1) / n2)
+        ms = max_over_ranks(pg, timed_steps(n2))
+        # the pipeline's three resources, each alone: host-to-device copies of
+        # one step, the range GEMMs, the device-to-host read-back
+        Ad, Bd, Cdd = sets[0]
+        h2d_ms = timed_alone(lambda: (Ad.copy_(Ah, non_blocking=True), Bd.copy_(Bh, non_blocking=True),
+                                      Cdd.copy_(Ch, non_blocking=True)))
+        gemm_ms = timed_alone(lambda: [bg.batched_gemm_grouped(pl, Ad, Bd, Cdd, batch.alpha,
+                                                               batch.beta) for pl, _ in chunks])
+        d2h_ms = timed_alone(lambda: Co.copy_(Cdd, non_blocking=True))
+        hb, db = Ah.nbytes + Bh.nbytes + Ch.nbytes, Co.nbytes
+        del sets  # set 0 is (A, B, Cd): its copies wrote the same values A and B held
         e2e = {"value": job_flops / (ms * 1e-3) / 1e12, "unit": UNIT,
-               "h2d_bytes_per_step": int(Ah.nbytes + Bh.nbytes + Ch.nbytes),
-               "d2h_bytes_per_step": int(Co.nbytes), "ms_per_step": ms,
-               "pipeline": f"{len(chunks)} instance ranges, copies overlapped with the GEMM"}
+               "h2d_bytes_per_step": int(hb), "d2h_bytes_per_step": int(db), "ms_per_step": ms,
+               "pipeline": (f"{len(chunks)} instance ranges on three streams (copies in, range "
+                            f"GEMMs, read-back), two device buffer sets alternating between steps"),
+               "breakdown": {"h2d_alone_ms": h2d_ms, "h2d_gbs": hb / (h2d_ms * 1e-3) / 1e9,
+                             "gemm_alone_ms": gemm_ms, "d2h_alone_ms": d2h_ms,
+                             "d2h_gbs": db / (d2h_ms * 1e-3) / 1e9,
+                             "bound": "host link" if h2d_ms >= max(gemm_ms, d2h_ms) else
+                                      ("GEMM" if gemm_ms >= d2h_ms else "read-back")}}
 
     # --- the paper's design on this GPU, for context: one cuBLAS GEMM per instance
     lib_base = None

@@ -185,6 +185,10 @@ struct ClassInfo {
   std::vector<std::pair<int, double>> tried;
 };
 
+// Route of a class that the split path computes (ClassInfo::prog, and the
+// autotune cache's "prog" entry for split-mode keys).
+constexpr int PROG_SPLIT = -2;
+
 struct bg_plan {
   int device = 0;
   bg_dtype dtype = BG_R64;
@@ -373,7 +377,8 @@ std::map<std::string, int> read_cache(const char* path) {
     const char* pp = strstr(q2, "\"prog\":");
     if (!pp) continue;
     int prog = -1;
-    if (sscanf(pp + 7, "%d", &prog) == 1 && prog >= 0 && prog < PROG_COUNT) out[key] = prog;
+    if (sscanf(pp + 7, "%d", &prog) == 1 && ((prog >= 0 && prog < PROG_COUNT) || prog == PROG_SPLIT))
+      out[key] = prog;
   }
   fclose(f);
   return out;
@@ -533,10 +538,88 @@ void destroy_plan(bg_plan* p) {
   delete p;
 }
 
+// Times the split path (slicer and tensor-core GEMM) on a compact zeroed sample
+// of one class (at most about 64 MiB per operand), scaled to the whole class
+// by flops. Returns ms (median of 3 runs after one warm-up).
+bg_status time_class_split(bg_plan* p, int cls, cudaStream_t st, double* ms) {
+  const int64_t esz = p->dtype == BG_C128 ? 16 : 8;
+  const bool herk = (p->flags & BG_PLAN_HERK) != 0;
+  std::vector<bg_instance> sub;
+  int64_t la = 0, lb = 0, lc = 0;
+  double sflops = 0, cflops = 0;
+  for (int64_t i = 0; i < p->count; ++i) {
+    if (p->inst_class[i] != cls) continue;
+    const bg_instance& t = p->table[i];
+    cflops += (double)t.m * t.n * t.k;
+    const int64_t a = std::max<int64_t>(1, t.m) * std::max<int64_t>(1, t.k);
+    const int64_t b = std::max<int64_t>(1, t.k) * std::max<int64_t>(1, t.n);
+    const int64_t c = std::max<int64_t>(1, t.m) * std::max<int64_t>(1, t.n);
+    if (!sub.empty() && (la + a) * esz > (64ll << 20)) continue;
+    sub.push_back(bg_instance{t.m, t.n, t.k, std::max<int64_t>(1, t.m),
+                              std::max<int64_t>(1, t.k), std::max<int64_t>(1, t.m), la, lb, lc});
+    sflops += (double)t.m * t.n * t.k;
+    la += a;
+    lb += b;
+    lc += c;
+  }
+  *ms = 0;
+  if (sub.empty() || sflops == 0) return BG_OK;
+  DeviceCtx* ctx;
+  bg_status rs = get_ctx(&ctx);
+  if (rs != BG_OK) return rs;
+  SplitPlan* sp = nullptr;
+  rs = split_plan_create(&sp, p->dtype, p->prec, sub, nullptr, ctx->sms, false, st,
+                         &g_last_error, herk);
+  if (rs != BG_OK) return rs;
+  void *A = nullptr, *B = nullptr, *C = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<float> times;
+  do {
+    if (cudaMalloc(&A, la * esz) != cudaSuccess || cudaMalloc(&B, lb * esz) != cudaSuccess ||
+        cudaMalloc(&C, lc * esz) != cudaSuccess) {
+      rs = fail(BG_ERR_NOMEM, "autotune scratch allocation failed");
+      break;
+    }
+    cudaMemsetAsync(A, 0, la * esz, st);
+    cudaMemsetAsync(B, 0, lb * esz, st);
+    cudaMemsetAsync(C, 0, lc * esz, st);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    Scalars s;
+    s.alpha_re = 1.0; s.alpha_im = 0.0; s.beta_re = 0.0; s.beta_im = 0.0;
+    s.alpha_zero = 0; s.beta_zero = 1;
+    for (int r = 0; r < 4 && rs == BG_OK; ++r) {
+      cudaEventRecord(e0, st);
+      rs = split_plan_run(sp, A, B, C, s, ctx->d_err, st, &g_last_error);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float tm = 0;
+      cudaEventElapsedTime(&tm, e0, e1);
+      if (r > 0) times.push_back(tm);
+    }
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cudaFree(A); cudaFree(B); cudaFree(C);
+  split_plan_destroy(sp);
+  if (rs != BG_OK) return rs;
+  std::sort(times.begin(), times.end());
+  *ms = times.empty() ? 0.0 : times[times.size() / 2] * cflops / sflops;
+  return BG_OK;
+}
+
 // Chooses one FP64 program per class (default or autotuned) and builds the
 // device work list of the FP64 path.
+//
+// Split mode: without BG_PLAN_AUTOTUNE every class goes to the split path and
+// no FP64 work is built. With it, each class's split time is measured beside
+// its best FP64 program's, and the class is computed by whichever is faster
+// (the FP64 path is never less accurate than the split modes); the choice is
+// cached like the FP64 programs (key with the split mode and slice count).
 bg_status build_fp64_schedule(bg_plan* p, const char* cache_path, cudaStream_t st) {
   const bool tune = (p->flags & BG_PLAN_AUTOTUNE) != 0;
+  const bool split = p->prec.mode != BG_MODE_FP64;
   const bool use_cache = (p->flags & BG_PLAN_USE_CACHE) != 0 && cache_path;
   std::map<std::string, int> cache;
   if (use_cache) cache = read_cache(cache_path);
@@ -562,13 +645,18 @@ bg_status build_fp64_schedule(bg_plan* p, const char* cache_path, cudaStream_t s
       if (q == PROG_R64_SMALL || q == PROG_C128_SMALL) def = q;
     if (std::find(cand.begin(), cand.end(), def) == cand.end() && !cand.empty()) def = cand[0];
     ci.prog = def;
+    if (split && !tune) {
+      ci.prog = PROG_SPLIT;
+      continue;
+    }
     const std::string key = class_key(p->dtype, p->prec, ci);
     if (use_cache && cache.count(key) &&
-        std::find(cand.begin(), cand.end(), cache[key]) != cand.end()) {
+        (std::find(cand.begin(), cand.end(), cache[key]) != cand.end() ||
+         (split && cache[key] == PROG_SPLIT))) {
       ci.prog = cache[key];
       continue;
     }
-    if (tune && cand.size() > 1) {
+    if (tune && (cand.size() > 1 || split)) {
       double best = 1e300;
       for (int q : cand) {
         double ms = 0;
@@ -578,6 +666,16 @@ bg_status build_fp64_schedule(bg_plan* p, const char* cache_path, cudaStream_t s
         if (ms < best) {
           best = ms;
           ci.prog = q;
+          ci.ms = ms;
+        }
+      }
+      if (split) {
+        double ms = 0;
+        bg_status s = time_class_split(p, (int)c, st, &ms);
+        if (s != BG_OK) return s;
+        ci.tried.push_back({PROG_SPLIT, ms});
+        if (ms <= best) {
+          ci.prog = PROG_SPLIT;
           ci.ms = ms;
         }
       }
@@ -597,7 +695,7 @@ bg_status build_fp64_schedule(bg_plan* p, const char* cache_path, cudaStream_t s
   }
   std::vector<int64_t> live;
   for (int64_t i = 0; i < p->count; ++i)
-    if (p->table[i].m > 0 && p->table[i].n > 0) live.push_back(i);
+    if (p->table[i].m > 0 && p->table[i].n > 0 && prog_of[i] != PROG_SPLIT) live.push_back(i);
   std::vector<WorkItem> items;
   std::vector<int32_t> order;
   build_items(live, mnk, prog_of, &items, &order, (p->flags & BG_PLAN_HERK) != 0);
@@ -781,14 +879,25 @@ bg_status batched_gemm_plan(bg_plan** out, bg_dtype dtype, int64_t count,
     }
     p->launches_per_call = p->n_items > 0 ? 1 : 0;
   } else {
-    s = split_plan_create(&p->split, dtype, pr, p->table, p->d_table, ctx->sms,
-                          (flags & BG_PLAN_AUTOTUNE) != 0, st, &g_last_error, herk);
-    if (s != BG_OK) {
+    // each class to the split path, or (autotuned) to the FP64 path where that is faster
+    if ((s = build_fp64_schedule(p, cache_path, st)) != BG_OK) {
       destroy_plan(p);
       return s;
     }
-    p->workspace_bytes += split_plan_workspace(p->split);
-    p->launches_per_call = split_plan_launches(p->split);
+    std::vector<bg_instance> sub;
+    for (int64_t i = 0; i < count; ++i)
+      if (p->classes[p->inst_class[i]].prog == PROG_SPLIT) sub.push_back(p->table[i]);
+    if (!sub.empty()) {
+      s = split_plan_create(&p->split, dtype, pr, sub, nullptr, ctx->sms, false, st,
+                            &g_last_error, herk);
+      if (s != BG_OK) {
+        destroy_plan(p);
+        return s;
+      }
+      p->workspace_bytes += split_plan_workspace(p->split);
+    }
+    p->launches_per_call =
+        (p->split ? split_plan_launches(p->split) : 0) + (p->n_items > 0 ? 1 : 0);
   }
   *out = p;
   return BG_OK;
@@ -819,8 +928,21 @@ static bg_status run_grouped_direct(bg_plan* p, const void* A, const void* B, vo
   DeviceCtx* ctx;
   bg_status s = get_ctx(&ctx);
   if (s != BG_OK) return s;
-  return split_plan_run(p->split, A, B, C, sc, ctx->d_err, st, &g_last_error,
-                        ev ? ev + 1 : nullptr);
+  if (p->split) {
+    s = split_plan_run(p->split, A, B, C, sc, ctx->d_err, st, &g_last_error,
+                       ev ? ev + 1 : nullptr);
+    if (s != BG_OK) return s;
+  } else if (ev) {
+    BG_CUDA(cudaEventRecord(ev[1], st), "profiling event record");
+  }
+  if (p->n_items > 0) {
+    // classes the autotuner gave to the FP64 path (timed with the GEMM slot)
+    cudaError_t e = launch_fp64_table(p->dtype, p->d_table, p->d_order, p->d_items, p->n_items, A,
+                                      B, C, sc, p->grid, st, (p->flags & BG_PLAN_HERK) != 0);
+    if (e != cudaSuccess) return cuda_fail(e, "grouped FP64 launch");
+    if (ev) BG_CUDA(cudaEventRecord(ev[2], st), "profiling event record");
+  }
+  return BG_OK;
 }
 
 bg_status batched_gemm_grouped(const bg_plan* plan, const void* A_base, const void* B_base,
@@ -1078,7 +1200,7 @@ bg_status bg_plan_kernel_times(const bg_plan* plan, int32_t reset, double* total
 bg_status bg_plan_get_info(const bg_plan* p, bg_plan_info* out) {
   if (!p || !out) return fail(BG_ERR_INVALID_ARG, "null pointer");
   out->count = p->count;
-  out->work_items = p->split ? split_plan_items(p->split) : p->n_items;
+  out->work_items = (p->split ? split_plan_items(p->split) : 0) + p->n_items;
   out->launches_per_call = p->launches_per_call;
   out->classes = (int32_t)p->classes.size();
   out->workspace_bytes = p->workspace_bytes;
@@ -1107,8 +1229,9 @@ bg_status bg_plan_describe(const bg_plan* p, char* buf, size_t len, size_t* need
              (ci.prog >= 0 && ci.prog < PROG_COUNT) ? names[ci.prog] : "split", ci.ms);
     s += tmp;
     for (size_t t = 0; t < ci.tried.size(); ++t) {
+      const int q = ci.tried[t].first;
       snprintf(tmp, sizeof tmp, "%s{\"program\": \"%s\", \"ms\": %.6f}", t ? ", " : "",
-               names[ci.tried[t].first], ci.tried[t].second);
+               (q >= 0 && q < PROG_COUNT) ? names[q] : "split", ci.tried[t].second);
       s += tmp;
     }
     s += "]}";

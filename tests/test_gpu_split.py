@@ -41,6 +41,34 @@ def test_size_mix_uniform_reduced(gpu, s):
     assert e.max() <= TOL_SPLIT[s], (s, e.max())
 
 
+@pytest.mark.parametrize("s", [3, 9])
+def test_autotuned_plan_routes_and_matches_oracle(gpu, s, tmp_path):
+    """BG_PLAN_AUTOTUNE in split mode times each size class on the split path and
+    on the FP64 path and gives the class to the faster one; whatever the routes,
+    every instance meets the mode's tolerance, and a cached second plan takes
+    the same routes without timing."""
+    import json
+    b = synth.size_mix_loguniform(count=300)
+    cache = str(tmp_path / "tune.json")
+    flags = bg.BG_PLAN_AUTOTUNE | bg.BG_PLAN_USE_CACHE
+    C, plan = run_grouped(b, split(s), flags, cache_path=cache)
+    d = json.loads(plan.describe())
+    routes = {tuple(c["bucket"]): c["program"] for c in d["classes"]}
+    for c in d["classes"]:
+        names = [x["program"] for x in c["tried"]]
+        assert "split" in names and len(names) >= 2  # both paths were timed
+    e = errors(b, host(C), oracle_batch(b))
+    assert e.max() <= TOL_SPLIT[s], (s, e.max())
+    n_split = sum(1 for v in routes.values() if v == "split")
+    want = 1 + (1 if n_split else 0) + (1 if n_split < len(routes) else 0)
+    assert plan.info()["launches_per_call"] == (want if n_split else want - 1)
+    C2, plan2 = run_grouped(b, split(s), flags, cache_path=cache)
+    d2 = json.loads(plan2.describe())
+    assert {tuple(c["bucket"]): c["program"] for c in d2["classes"]} == routes
+    assert all(c["tried"] == [] for c in d2["classes"])
+    assert np.array_equal(host(C2), host(C))
+
+
 def test_error_decreases_with_slices(gpu):
     b = synth.size_mix_loguniform(count=100)
     ref = oracle_batch(b)

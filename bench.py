@@ -44,10 +44,10 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # divided by that batch's algorithmic bytes (990601216): a full launch's traffic
 # is this ratio times its own algorithmic bytes. Valid only while the split kernel sources
 # hash to NCU_SOURCES_SHA; otherwise the traffic is reported as null.
-NCU_TRAFFIC_PER_BYTE = {"split9": {"gemm": 1.806581e9 / 990601216.0,
+NCU_TRAFFIC_PER_BYTE = {"split9": {"gemm": 1.805783e9 / 990601216.0,
                                    "slicer": 1.810911e9 / 990601216.0}}
 NCU_SOURCES = ("split.cu", "split_common.cuh", "split_gemm.cuh", "split_gemm_r64.cu")
-NCU_SOURCES_SHA = "1093ee09442d5f89"
+NCU_SOURCES_SHA = "6f32ba6f69760916"
 
 
 def split_sources_sha() -> str:
@@ -958,6 +958,28 @@ def main():
         res[m] = {"ms_per_step": ms, "steps": steps,
                   "value": job_flops / (ms * 1e-3) / 1e12,
                   "kernel_ms": [kt[0] / max(calls, 1), kt[1] / max(calls, 1)]}
+        del Cm
+
+    # --- split modes with BG_PLAN_AUTOTUNE: each size class on the split path or
+    # on the FP64 path, whichever the plan measured faster
+    for m in modes:
+        if m == "fp64":
+            continue
+        tp = bg.batched_gemm_plan(batch.dtype, batch.table, bg.precision("split", int(m[5:])),
+                                  bg.BG_PLAN_AUTOTUNE | bg.BG_PLAN_USE_CACHE, cache)
+        Cm = C0.clone()
+        ms = _time_calls(lambda: bg.batched_gemm_grouped(tp, A, B, Cm, batch.alpha, batch.beta),
+                         args.steps, args.warmup)
+        Cm.copy_(C0)
+        bg.batched_gemm_grouped(tp, A, B, Cm, batch.alpha, batch.beta)
+        err = sample_errors(batch, Cm.cpu().numpy(), ref) if ref is not None else None
+        routes = {str(c["bucket"][0]): c["program"] for c in json.loads(tp.describe())["classes"]}
+        ms = max_over_ranks(pg, ms)
+        res[m]["autotuned"] = {"ms_per_step": ms, "value": job_flops / (ms * 1e-3) / 1e12,
+                               "unit": UNIT, "routes": routes,
+                               "default_over_tuned": res[m]["ms_per_step"] / ms,
+                               "max_err_vs_oracle_sample": err}
+        tp.close()
         del Cm
 
     # --- roofline of the dominant kernel of each mode

@@ -957,7 +957,7 @@ def main():
         log(f"{m}: {ms:.3f} ms/step")
         res[m] = {"ms_per_step": ms, "steps": steps,
                   "value": job_flops / (ms * 1e-3) / 1e12,
-                  "kernel_ms": [kt[0] / max(calls, 1), kt[1] / max(calls, 1)]}
+                  "kernel_ms": [x / max(calls, 1) for x in kt]}
         del Cm
 
     # --- split modes with BG_PLAN_AUTOTUNE: each size class on the split path or
@@ -999,8 +999,13 @@ def main():
         else:
             s = int(m[5:])
             pairs = s * (s + 1) // 2
+            sp = json.loads(plans[m].describe()).get("split", {})
+            # instances on the small-instance kernel (real, m, n, k <= 64) leave
+            # the tile GEMM and the slicer; the flops are real-GEMM flops (2 mnk)
+            small_fl = 2.0 * sp.get("small_mnk", 0.0)
+            small_ab = sp.get("small_ab_elems", 0.0)
             k_ms = r["kernel_ms"][1]
-            tf = pairs * flops
+            tf = pairs * (flops - small_fl)
             ach = tf / (k_ms * 1e-3) / 1e12
             pk_bf16 = pk["bf16_tflops"]
             r["roofline"] = {"kernel": "split_gemm_kernel (tcgen05)", "bound": "tensor",
@@ -1008,9 +1013,23 @@ def main():
                              "frac": ach / pk_bf16,
                              "traffic": (NCU_TRAFFIC_PER_BYTE[m]["gemm"] * batch.bytes_moved()
                                          if traffic_ok and m in NCU_TRAFFIC_PER_BYTE else None),
+                             "flops_per_launch": tf,
+                             "instances": batch.count - sp.get("small_instances", 0),
                              "peak_source": f"bf16 burst, {pk_src} (MEASURED_PEAKS.json)"}
+            if sp.get("small_instances", 0) > 0:
+                sm_ms = r["kernel_ms"][2]
+                sm_tf = pairs * small_fl / (sm_ms * 1e-3) / 1e12
+                # mma.sync BF16 issues 2048 flop/clk/SM, a quarter of tcgen05 (microbenchmark)
+                sm_pk = pk_bf16 / 4.0
+                r["small"] = {"kernel": "split_small_kernel (mma.sync)", "bound": "tensor",
+                              "instances": sp["small_instances"], "ms": sm_ms,
+                              "achieved": sm_tf, "peak": sm_pk, "unit": "TFLOP/s",
+                              "frac": sm_tf / sm_pk,
+                              "peak_source": "bf16 burst / 4 (mma.sync rate, 2048 of 8192 "
+                                             "flop/clk/SM)",
+                              "flops_per_launch": pairs * small_fl}
             sl_ms = r["kernel_ms"][0]
-            sl_bytes = ab_elems * (esz + 2.0 * s * (4.0 if batch.dtype == "c128" else 1.0))
+            sl_bytes = (ab_elems - small_ab) * (esz + 2.0 * s * (4.0 if batch.dtype == "c128" else 1.0))
             r["slicer"] = {"kernel": "split_slice_kernel", "bound": "hbm",
                            "achieved": sl_bytes / (sl_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
                            "unit": "GB/s",

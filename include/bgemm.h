@@ -108,7 +108,11 @@ enum {
   BG_PLAN_USE_CACHE = 2u,     /* read/write autotune results in the JSON file cache_path */
   BG_PLAN_CAPTURE_GRAPH = 4u, /* batched_gemm_grouped replays a captured CUDA graph */
   BG_PLAN_PROFILE = 8u,       /* record CUDA events around each kernel (bg_plan_kernel_times) */
-  BG_PLAN_HERK = 16u          /* Hermitian rank-k updates instead of Eq. (1), see below */
+  BG_PLAN_HERK = 16u,         /* Hermitian rank-k updates instead of Eq. (1), see below */
+  BG_PLAN_SPLIT_TILES = 32u   /* split mode: compute every instance with the digit-plane tile
+                                 kernels, also the small real ones (m, n, k <= 64) that
+                                 otherwise go to the fused small-instance kernel; results of
+                                 both stay within the split mode's error bound */
 };
 
 /* BG_PLAN_HERK. Sec. 3 builds the density matrix rho = Psi Psi^H of each
@@ -195,8 +199,12 @@ bg_status batched_gemm_plan(bg_plan** out, bg_dtype dtype, int64_t count,
 /* ---- Eq. (1), variable-size batch: run ------------------------------------
  * Computes every instance of the plan with A_base + a_off etc. (element
  * offsets from the plan's table). FP64 mode: one persistent launch that
- * walks the device work table. Split mode: exponent pass, slicing pass and
- * one persistent tensor-core launch. With BG_PLAN_CAPTURE_GRAPH the launches
+ * walks the device work table. Split mode: the slicing pass (line exponents
+ * and digit planes), one persistent tensor-core launch over the digit tiles
+ * and, for the real instances with m, n, k <= 64 (unless
+ * BG_PLAN_SPLIT_TILES), one fused small-instance launch that cuts the digits
+ * into shared memory itself; instances that an autotuned plan routed to the
+ * FP64 path add the FP64 launch. With BG_PLAN_CAPTURE_GRAPH the launches
  * are captured once into a CUDA graph keyed by (A_base, B_base, C_base,
  * alpha, beta) and replayed; a call with other pointers or scalars
  * re-captures. Calls on one plan must not overlap on the GPU (they share the
@@ -374,10 +382,12 @@ bg_status bg_plan_describe(const bg_plan* plan, char* buf, size_t len, size_t* n
  * library's own per-kernel timing, from CUDA events recorded on the call's
  * stream around each launch). Synchronises on the recorded events and writes,
  * for each kernel slot of one call (slot 0: the FP64 kernel, or the slicer in
- * split mode; slot 1: the split tensor-core GEMM), the summed milliseconds over
- * all calls since the last reset into total_ms[0..1] and the number of calls
- * into *calls. reset = 1 clears the sums after reading. Graph capture is not
- * used while profiling. */
+ * split mode; slot 1: the split tensor-core tile GEMM, plus the FP64 launch
+ * of classes an autotuned split plan gave to the FP64 path; slot 2: the
+ * split mode's small-instance kernel), the summed milliseconds over all calls
+ * since the last reset into total_ms[0..2] (an array of 3 doubles; unused
+ * slots read 0) and the number of calls into *calls. reset = 1 clears the
+ * sums after reading. Graph capture is not used while profiling. */
 bg_status bg_plan_kernel_times(const bg_plan* plan, int32_t reset, double* total_ms,
                                int64_t* calls);
 

@@ -29,6 +29,7 @@ BG_R64, BG_C128 = 0, 1
 BG_MODE_FP64, BG_MODE_SPLIT_BF16 = 0, 1
 BG_PLAN_AUTOTUNE, BG_PLAN_USE_CACHE, BG_PLAN_CAPTURE_GRAPH, BG_PLAN_PROFILE = 1, 2, 4, 8
 BG_PLAN_HERK = 16  # Hermitian rank-k updates C = alpha A A^H + beta C (lower triangle)
+BG_PLAN_SPLIT_TILES = 32  # split mode: no small-instance kernel (every instance on the tile kernels)
 
 STATUS = {0: "BG_OK", 1: "BG_ERR_INVALID_ARG", 2: "BG_ERR_UNSUPPORTED", 3: "BG_ERR_CUDA",
           4: "BG_ERR_NOMEM", 5: "BG_ERR_CAPTURE", 6: "BG_ERR_TIMEOUT"}
@@ -248,12 +249,14 @@ class Plan:
         return buf.value.decode()
 
     def kernel_times(self, reset: bool = False) -> tuple[list[float], int]:
-        """Summed per-kernel ms (slot 0, slot 1) and call count (plans made with BG_PLAN_PROFILE)."""
-        ms = (ctypes.c_double * 2)()
+        """Summed per-kernel ms and call count (plans made with BG_PLAN_PROFILE): slot 0
+        the slicer (FP64 mode: the FP64 kernel), slot 1 the tile GEMM, slot 2 the
+        small-instance kernel."""
+        ms = (ctypes.c_double * 3)()
         calls = ctypes.c_int64(0)
         _check(load_library().bg_plan_kernel_times(self.handle, 1 if reset else 0, ms,
                                                    ctypes.byref(calls)))
-        return [ms[0], ms[1]], calls.value
+        return [ms[0], ms[1], ms[2]], calls.value
 
     def close(self) -> None:
         if self.handle:

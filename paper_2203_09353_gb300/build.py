@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbgemm.so")
 
-SOURCES = ["api.cpp", "fp64.cu", "split.cu", "split_gemm_r64.cu", "split_gemm_c128.cu", "util.cu", "gate.cu",
+SOURCES = ["api.cpp", "fp64.cu", "split.cu", "split_gemm_r64.cu", "split_gemm_c128.cu",
+           "split_small.cu", "util.cu", "gate.cu",
            "noalloc.cu", "entropy.cu", "anneal.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

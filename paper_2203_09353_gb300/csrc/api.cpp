@@ -237,9 +237,10 @@ struct bg_plan {
   int64_t workspace_bytes = 0;
   int launches_per_call = 0;
   // profiling: per call three events (start, after slot 0, after slot 1)
-  std::vector<std::array<cudaEvent_t, 3>> prof_events;
+  // per profiled call: start, after slot 0, after slot 2, after slot 1
+  std::vector<std::array<cudaEvent_t, 4>> prof_events;
   size_t prof_used = 0;
-  double prof_ms[2] = {0.0, 0.0};
+  double prof_ms[3] = {0.0, 0.0, 0.0};
   int64_t prof_calls = 0;
 };
 
@@ -569,7 +570,7 @@ bg_status time_class_split(bg_plan* p, int cls, cudaStream_t st, double* ms) {
   if (rs != BG_OK) return rs;
   SplitPlan* sp = nullptr;
   rs = split_plan_create(&sp, p->dtype, p->prec, sub, nullptr, ctx->sms, false, st,
-                         &g_last_error, herk);
+                         &g_last_error, herk, (p->flags & BG_PLAN_SPLIT_TILES) == 0);
   if (rs != BG_OK) return rs;
   void *A = nullptr, *B = nullptr, *C = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -848,7 +849,7 @@ bg_status batched_gemm_plan(bg_plan** out, bg_dtype dtype, int64_t count,
   if (count < 0) return fail(BG_ERR_INVALID_ARG, "negative count");
   if (count > INT32_MAX / 2) return fail(BG_ERR_INVALID_ARG, "count too large");
   if (count > 0 && !host_table) return fail(BG_ERR_INVALID_ARG, "host_table is NULL");
-  if (flags & ~31u) return fail(BG_ERR_INVALID_ARG, "unknown plan flags 0x%x", flags);
+  if (flags & ~63u) return fail(BG_ERR_INVALID_ARG, "unknown plan flags 0x%x", flags);
   const bool herk = (flags & BG_PLAN_HERK) != 0;
   for (int64_t i = 0; i < count; ++i)
     if ((s = check_instance(host_table[i], i, herk)) != BG_OK) return s;
@@ -889,7 +890,7 @@ bg_status batched_gemm_plan(bg_plan** out, bg_dtype dtype, int64_t count,
       if (p->classes[p->inst_class[i]].prog == PROG_SPLIT) sub.push_back(p->table[i]);
     if (!sub.empty()) {
       s = split_plan_create(&p->split, dtype, pr, sub, nullptr, ctx->sms, false, st,
-                            &g_last_error, herk);
+                            &g_last_error, herk, (flags & BG_PLAN_SPLIT_TILES) == 0);
       if (s != BG_OK) {
         destroy_plan(p);
         return s;
@@ -908,7 +909,7 @@ static bg_status run_grouped_direct(bg_plan* p, const void* A, const void* B, vo
   cudaEvent_t* ev = nullptr;
   if (p->flags & BG_PLAN_PROFILE) {
     if (p->prof_used == p->prof_events.size()) {
-      std::array<cudaEvent_t, 3> t{};
+      std::array<cudaEvent_t, 4> t{};
       for (auto& e : t) BG_CUDA(cudaEventCreate(&e), "profiling event");
       p->prof_events.push_back(t);
     }
@@ -919,10 +920,8 @@ static bg_status run_grouped_direct(bg_plan* p, const void* A, const void* B, vo
     cudaError_t e = launch_fp64_table(p->dtype, p->d_table, p->d_order, p->d_items, p->n_items, A,
                                       B, C, sc, p->grid, st, (p->flags & BG_PLAN_HERK) != 0);
     if (e != cudaSuccess) return cuda_fail(e, "grouped FP64 launch");
-    if (ev) {
-      BG_CUDA(cudaEventRecord(ev[1], st), "profiling event record");
-      BG_CUDA(cudaEventRecord(ev[2], st), "profiling event record");
-    }
+    if (ev)
+      for (int i = 1; i < 4; ++i) BG_CUDA(cudaEventRecord(ev[i], st), "profiling event record");
     return BG_OK;
   }
   DeviceCtx* ctx;
@@ -933,14 +932,14 @@ static bg_status run_grouped_direct(bg_plan* p, const void* A, const void* B, vo
                        ev ? ev + 1 : nullptr);
     if (s != BG_OK) return s;
   } else if (ev) {
-    BG_CUDA(cudaEventRecord(ev[1], st), "profiling event record");
+    for (int i = 1; i < 4; ++i) BG_CUDA(cudaEventRecord(ev[i], st), "profiling event record");
   }
   if (p->n_items > 0) {
     // classes the autotuner gave to the FP64 path (timed with the GEMM slot)
     cudaError_t e = launch_fp64_table(p->dtype, p->d_table, p->d_order, p->d_items, p->n_items, A,
                                       B, C, sc, p->grid, st, (p->flags & BG_PLAN_HERK) != 0);
     if (e != cudaSuccess) return cuda_fail(e, "grouped FP64 launch");
-    if (ev) BG_CUDA(cudaEventRecord(ev[2], st), "profiling event record");
+    if (ev) BG_CUDA(cudaEventRecord(ev[3], st), "profiling event record");
   }
   return BG_OK;
 }
@@ -1178,20 +1177,21 @@ bg_status bg_plan_kernel_times(const bg_plan* plan, int32_t reset, double* total
   bg_plan* p = const_cast<bg_plan*>(plan);
   for (size_t i = 0; i < p->prof_used; ++i) {
     cudaEvent_t* ev = p->prof_events[i].data();
-    BG_CUDA(cudaEventSynchronize(ev[2]), "profiling event sync");
-    float a = 0, b = 0;
+    BG_CUDA(cudaEventSynchronize(ev[3]), "profiling event sync");
+    float a = 0, b = 0, c = 0;
     BG_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]), "profiling elapsed");
-    BG_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]), "profiling elapsed");
+    BG_CUDA(cudaEventElapsedTime(&c, ev[1], ev[2]), "profiling elapsed");
+    BG_CUDA(cudaEventElapsedTime(&b, ev[2], ev[3]), "profiling elapsed");
     p->prof_ms[0] += a;
     p->prof_ms[1] += b;
+    p->prof_ms[2] += c;
     p->prof_calls++;
   }
   p->prof_used = 0;
-  total_ms[0] = p->prof_ms[0];
-  total_ms[1] = p->prof_ms[1];
+  for (int i = 0; i < 3; ++i) total_ms[i] = p->prof_ms[i];
   *calls = p->prof_calls;
   if (reset) {
-    p->prof_ms[0] = p->prof_ms[1] = 0.0;
+    p->prof_ms[0] = p->prof_ms[1] = p->prof_ms[2] = 0.0;
     p->prof_calls = 0;
   }
   return BG_OK;
@@ -1424,7 +1424,7 @@ bg_status batched_entropy(const bg_plan* plan, const void* states, double* entro
   cudaEvent_t* ev = nullptr;
   if (p->flags & BG_PLAN_PROFILE) {
     if (p->prof_used == p->prof_events.size()) {
-      std::array<cudaEvent_t, 3> tev{};
+      std::array<cudaEvent_t, 4> tev{};
       for (auto& e : tev) BG_CUDA(cudaEventCreate(&e), "profiling event");
       p->prof_events.push_back(tev);
     }
@@ -1434,11 +1434,14 @@ bg_status batched_entropy(const bg_plan* plan, const void* states, double* entro
   const double one[2] = {1.0, 0.0}, zero[2] = {0.0, 0.0};
   bg_status s = batched_gemm_grouped(p->gram, states, nullptr, p->d_gram, one, zero, stream);
   if (s != BG_OK) return s;
-  if (ev) BG_CUDA(cudaEventRecord(ev[1], st), "profiling event record");
+  if (ev) {
+    BG_CUDA(cudaEventRecord(ev[1], st), "profiling event record");
+    BG_CUDA(cudaEventRecord(ev[2], st), "profiling event record");
+  }
   cudaError_t e = launch_entropy_eig(p->d_gram, p->count, p->ent_n, p->d_tri_d, p->d_tri_e,
                                      entropy, eigenvalues, st);
   if (e != cudaSuccess) return cuda_fail(e, "entropy eigenvalue launch");
-  if (ev) BG_CUDA(cudaEventRecord(ev[2], st), "profiling event record");
+  if (ev) BG_CUDA(cudaEventRecord(ev[3], st), "profiling event record");
   return BG_OK;
 }
 

@@ -445,6 +445,7 @@ struct SplitPlan {
   size_t smem = 0;
   bool chain = false;
   bool herk = false;       // Hermitian rank-k updates (B = A^H, lower triangle)
+  bool small_ok = false;   // real instances with m, n, k <= 64 go to the small-instance kernel
   int sms = 0;
   int64_t count = 0;
   // device
@@ -455,6 +456,10 @@ struct SplitPlan {
   SInst* d_inst = nullptr;       // instances (chain: walkers)
   SInst* d_pool = nullptr;       // chain: pool entries
   int32_t* d_order = nullptr;    // A side order (== B side order except chain)
+  int32_t* d_small = nullptr;    // instances computed by the small-instance kernel
+  SmallItem* d_small_items = nullptr;
+  int64_t n_small = 0, n_small_items = 0;
+  double small_mnk = 0, small_ab = 0;  // sum of m n k and of m k + k n over small instances
   int32_t* d_pool_order = nullptr;
   int64_t* d_pool_tile0 = nullptr;
   int32_t* d_pool_blk0 = nullptr;
@@ -464,7 +469,7 @@ struct SplitPlan {
   int32_t* metaA = nullptr;
   int32_t* metaB = nullptr;
   int64_t bytes = 0;
-  int grid_slice = 0, grid_gemm = 0;
+  int grid_slice = 0, grid_gemm = 0, grid_small = 0;
   std::vector<int64_t> key;  // fixed-size plan cache key
   std::string desc;
 };
@@ -493,6 +498,8 @@ void split_plan_destroy(SplitPlan* p) {
   cudaFree(p->d_inst);
   cudaFree(p->d_pool);
   cudaFree(p->d_order);
+  cudaFree(p->d_small);
+  cudaFree(p->d_small_items);
   cudaFree(p->d_pool_order);
   cudaFree(p->d_pool_tile0);
   cudaFree(p->d_pool_blk0);
@@ -504,8 +511,10 @@ void split_plan_destroy(SplitPlan* p) {
 }
 
 int64_t split_plan_workspace(const SplitPlan* p) { return p ? p->bytes : 0; }
-int split_plan_launches(const SplitPlan* p) { return p ? 2 : 0; }
-int64_t split_plan_items(const SplitPlan* p) { return p ? p->n_units : 0; }
+int split_plan_launches(const SplitPlan* p) {
+  return p ? (p->n_jobs > 0) + (p->n_units > 0) + (p->n_small > 0) : 0;
+}
+int64_t split_plan_items(const SplitPlan* p) { return p ? p->n_units + p->n_small : 0; }
 int split_plan_beta_bits(const SplitPlan* p) { return p ? p->beta : 0; }
 std::string split_plan_describe(const SplitPlan* p) { return p ? p->desc : "null"; }
 
@@ -579,6 +588,8 @@ struct HostTables {
   std::vector<int32_t> order;
   std::vector<SliceJob> jobs;
   std::vector<SplitUnit> units;
+  std::vector<int32_t> small;  // instances for the small-instance kernel
+  std::vector<SmallItem> small_items;
   int64_t tileA = 0, tileB = 0, n_jobs_A = 0;
   int32_t blkA = 0, blkB = 0;
 };
@@ -593,12 +604,38 @@ static void make_tables(const SplitPlan* p, const std::vector<bg_instance>& tabl
     inst[i] = SInst{t.a_off, t.b_off, t.c_off, t.lda, t.ldb, t.ldc, (int32_t)t.m, (int32_t)t.n,
                     (int32_t)t.k, 0};
   }
-  // group instances of identical shape (packing needs equal shapes)
+  // group instances of identical shape (packing needs equal shapes); small
+  // real instances go to their own kernel
   std::map<std::array<int64_t, 3>, std::vector<int32_t>> groups;
+  std::vector<int32_t> small;
   for (size_t i = 0; i < table.size(); ++i) {
     const bg_instance& t = table[i];
     if (t.m == 0 || t.n == 0) continue;
+    if (p->small_ok && !cplx && !p->herk && split_small_route(s, t.m, t.n, t.k)) {
+      small.push_back((int32_t)i);
+      continue;
+    }
     groups[{t.m, t.n, t.k}].push_back((int32_t)i);
+  }
+  // small instances by padded edge (64, 32, 16), largest first within an
+  // edge; work items of as many instances as the kernel runs side by side
+  auto edge = [&](int32_t i) {
+    const int64_t e = std::max(table[i].m, std::max(table[i].n, table[i].k));
+    return e <= 16 ? 16 : e <= 32 ? 32 : 64;
+  };
+  std::stable_sort(small.begin(), small.end(), [&](int32_t a, int32_t b) {
+    const int ea = edge(a), eb = edge(b);
+    if (ea != eb) return ea > eb;
+    return table[a].m * table[a].n * table[a].k > table[b].m * table[b].n * table[b].k;
+  });
+  std::vector<SmallItem> small_items;
+  for (size_t i = 0; i < small.size();) {
+    const int e = edge(small[i]);
+    const int ng = std::max(1, split_small_groups(s, e));
+    size_t j = i;
+    while (j < small.size() && j - i < (size_t)ng && edge(small[j]) == e) ++j;
+    small_items.push_back(SmallItem{(int32_t)i, (int16_t)(j - i), (int16_t)e});
+    i = j;
   }
   std::vector<int32_t> order;
   std::vector<SliceJob> jobsA, jobsB;
@@ -703,6 +740,8 @@ static void make_tables(const SplitPlan* p, const std::vector<bg_instance>& tabl
   out->order = std::move(order);
   out->jobs = std::move(jobs);
   out->units = std::move(units);
+  out->small = std::move(small);
+  out->small_items = std::move(small_items);
   out->tileA = tileA;
   out->tileB = tileB;
   out->blkA = blkA;
@@ -721,6 +760,13 @@ static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& t
   p->n_jobs = (int64_t)t.jobs.size();
   p->n_jobs_A = t.n_jobs_A;
   p->n_units = (int64_t)t.units.size();
+  p->n_small = (int64_t)t.small.size();
+  p->n_small_items = (int64_t)t.small_items.size();
+  for (int32_t i : t.small) {
+    const bg_instance& x = table[i];
+    p->small_mnk += (double)x.m * x.n * x.k;
+    p->small_ab += (double)x.m * x.k + (double)x.k * x.n;
+  }
   p->count = (int64_t)table.size();
   const size_t btile = (size_t)p->bn * kLineBytes;
   cudaError_t e;
@@ -728,6 +774,8 @@ static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& t
       (e = dput(&p->d_units, t.units, &p->bytes)) != cudaSuccess ||
       (e = dput(&p->d_inst, t.inst, &p->bytes)) != cudaSuccess ||
       (e = dput(&p->d_order, t.order, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_small, t.small, &p->bytes)) != cudaSuccess ||
+      (e = dput(&p->d_small_items, t.small_items, &p->bytes)) != cudaSuccess ||
       (e = dalloc(reinterpret_cast<void**>(&p->tilesA), (size_t)tileA * kATileBytes, &p->bytes)) !=
           cudaSuccess ||
       (e = dalloc(reinterpret_cast<void**>(&p->tilesB), (size_t)tileB * btile, &p->bytes)) !=
@@ -749,13 +797,15 @@ static bg_status build_instances(SplitPlan* p, const std::vector<bg_instance>& t
 }
 
 static void finish_desc(SplitPlan* p) {
-  char buf[512];
+  char buf[1024];
   snprintf(buf, sizeof buf,
            "{\"slices\": %d, \"beta_bits\": %d, \"pairs\": %d, \"tile\": [%d, %d, %d], "
            "\"kpass_kblocks\": %d, \"a_ring_groups\": %d, \"smem_bytes\": %zu, \"units\": %lld, "
-           "\"slice_jobs\": %lld, \"workspace_bytes\": %lld}",
+           "\"slice_jobs\": %lld, \"small_instances\": %lld, \"small_items\": %lld, "
+           "\"small_mnk\": %.17g, \"small_ab_elems\": %.17g, \"workspace_bytes\": %lld}",
            p->s, p->beta, p->s * (p->s + 1) / 2, BM, p->bn, BK, p->kpass, p->a_groups, p->smem,
-           (long long)p->n_units, (long long)p->n_jobs, (long long)p->bytes);
+           (long long)p->n_units, (long long)p->n_jobs, (long long)p->n_small,
+           (long long)p->n_small_items, p->small_mnk, p->small_ab, (long long)p->bytes);
   p->desc = buf;
 }
 
@@ -776,12 +826,14 @@ static void grids(SplitPlan* p) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, split_slice_kernel<9, 6>, kSliceThreads, 0);
   if (bps < 1) bps = 1;
   p->grid_slice = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)p->sms * bps, p->n_jobs));
+  if (p->n_small_items > 0)
+    p->grid_small = (int)std::max<int64_t>(1, std::min<int64_t>(p->sms, p->n_small_items));
 }
 
 bg_status split_plan_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr,
                             const std::vector<bg_instance>& table, const int64_t* d_table,
                             int sms, bool autotune, cudaStream_t st, std::string* err,
-                            bool herk) {
+                            bool herk, bool small_kernel) {
   (void)d_table;
   (void)autotune;
   (void)st;
@@ -791,6 +843,7 @@ bg_status split_plan_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr
     return BG_ERR_INVALID_ARG;
   }
   p->herk = herk;
+  p->small_ok = small_kernel && split_small_supported(p->s, p->beta);
   bg_status s = build_instances(p, table, err);
   if (s != BG_OK) {
     split_plan_destroy(p);
@@ -844,6 +897,25 @@ static cudaError_t launch_slicer(SplitPlan* p, const SliceJob* jobs, int64_t njo
   return cudaGetLastError();
 }
 
+// The small-instance kernel reads A and B itself (no slicer pass).
+static cudaError_t launch_small(SplitPlan* p, const void* A, const void* B, void* C,
+                                const Scalars& sc, cudaStream_t st) {
+  if (p->n_small <= 0) return cudaSuccess;
+  SmallArgs g;
+  g.inst = p->d_inst;
+  g.ids = p->d_small;
+  g.items = p->d_small_items;
+  g.nitems = p->n_small_items;
+  g.A = static_cast<const double*>(A);
+  g.B = static_cast<const double*>(B);
+  g.C = static_cast<double*>(C);
+  g.sc = sc;
+  g.skip_product = sc.alpha_zero;
+  const cudaError_t e = launch_split_small(p->s, p->grid_small, st, g);
+  count_launch();
+  return e;
+}
+
 static cudaError_t launch_gemm(SplitPlan* p, void* C, const Scalars& sc, const int32_t* idx,
                                int* d_err, cudaStream_t st) {
   if (p->n_units <= 0) return cudaSuccess;
@@ -886,9 +958,12 @@ bg_status split_plan_run(SplitPlan* p, const void* A, const void* B, void* C, co
     if (e != cudaSuccess) return cuda_err(err, e, "split slicer launch");
   }
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return cuda_err(err, e, "event");
+  e = launch_small(p, A, B, C, s, st);
+  if (e != cudaSuccess) return cuda_err(err, e, "split small-instance launch");
+  if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return cuda_err(err, e, "event");
   e = launch_gemm(p, C, s, nullptr, d_err, st);
   if (e != cudaSuccess) return cuda_err(err, e, "split GEMM launch");
-  if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return cuda_err(err, e, "event");
+  if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return cuda_err(err, e, "event");
   return BG_OK;
 }
 
@@ -944,6 +1019,7 @@ bg_status split_fixed_in_scratch(bg_dtype dt, const bg_precision& pr, int64_t m,
                                  std::string* err) {
   SplitPlan p;  // host object only: every device pointer below points into `scratch`
   if (!setup_common(&p, dt, pr, sms, err)) return BG_ERR_INVALID_ARG;
+  p.small_ok = split_small_supported(p.s, p.beta);
   std::vector<bg_instance> table((size_t)batch);
   for (int64_t i = 0; i < batch; ++i)
     table[i] = bg_instance{m, n, k, lda, ldb, ldc, i * sA, i * sB, i * sC};
@@ -960,6 +1036,8 @@ bg_status split_fixed_in_scratch(bg_dtype dt, const bg_precision& pr, int64_t m,
   const size_t o_units = off;  off += up(t.units.size() * sizeof(SplitUnit) + 1);
   const size_t o_inst = off;   off += up(t.inst.size() * sizeof(SInst) + 1);
   const size_t o_order = off;  off += up(t.order.size() * sizeof(int32_t) + 1);
+  const size_t o_small = off;  off += up(t.small.size() * sizeof(int32_t) + 1);
+  const size_t o_items = off;  off += up(t.small_items.size() * sizeof(SmallItem) + 1);
   const size_t o_ta = off;     off += up((size_t)t.tileA * kATileBytes);
   const size_t o_tb = off;     off += up((size_t)t.tileB * p.bn * kLineBytes);
   if (off > scratch_bytes) {
@@ -977,11 +1055,15 @@ bg_status split_fixed_in_scratch(bg_dtype dt, const bg_precision& pr, int64_t m,
   p.d_units = reinterpret_cast<SplitUnit*>(base + o_units);
   p.d_inst = reinterpret_cast<SInst*>(base + o_inst);
   p.d_order = reinterpret_cast<int32_t*>(base + o_order);
+  p.d_small = reinterpret_cast<int32_t*>(base + o_small);
+  p.d_small_items = reinterpret_cast<SmallItem*>(base + o_items);
   p.tilesA = base + o_ta;
   p.tilesB = base + o_tb;
   p.n_jobs = (int64_t)t.jobs.size();
   p.n_jobs_A = t.n_jobs_A;
   p.n_units = (int64_t)t.units.size();
+  p.n_small = (int64_t)t.small.size();
+  p.n_small_items = (int64_t)t.small_items.size();
   p.count = batch;
   cudaError_t e;
   // the scratch keeps the previous call's contents: clear the error word, the
@@ -993,7 +1075,9 @@ bg_status split_fixed_in_scratch(bg_dtype dt, const bg_precision& pr, int64_t m,
   const Piece pieces[] = {{o_jobs, t.jobs.data(), t.jobs.size() * sizeof(SliceJob)},
                           {o_units, t.units.data(), t.units.size() * sizeof(SplitUnit)},
                           {o_inst, t.inst.data(), t.inst.size() * sizeof(SInst)},
-                          {o_order, t.order.data(), t.order.size() * sizeof(int32_t)}};
+                          {o_order, t.order.data(), t.order.size() * sizeof(int32_t)},
+                          {o_small, t.small.data(), t.small.size() * sizeof(int32_t)},
+                          {o_items, t.small_items.data(), t.small_items.size() * sizeof(SmallItem)}};
   for (const Piece& pc : pieces)
     if (pc.bytes && (e = cudaMemcpyAsync(base + pc.off, pc.src, pc.bytes, cudaMemcpyHostToDevice,
                                          st)) != cudaSuccess)

@@ -28,7 +28,8 @@ int split_default_beta(int slices);
 
 bg_status split_plan_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr,
                             const std::vector<bg_instance>& table, const int64_t* d_table,
-                            int sms, bool autotune, cudaStream_t st, std::string* err, bool herk = false);
+                            int sms, bool autotune, cudaStream_t st, std::string* err, bool herk = false,
+                            bool small_kernel = true);
 bg_status split_chain_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr,
                              const std::vector<int64_t>& wn, const std::vector<int64_t>& woff,
                              const std::vector<int64_t>& pool_n,
@@ -41,7 +42,8 @@ int64_t split_plan_items(const SplitPlan* p);
 int split_plan_beta_bits(const SplitPlan* p);
 std::string split_plan_describe(const SplitPlan* p);
 
-// `ev` (optional): two events recorded after the slicer and after the GEMM.
+// `ev` (optional): three events recorded after the slicer, after the
+// small-instance kernel and after the tile GEMM.
 bg_status split_plan_run(SplitPlan* p, const void* A, const void* B, void* C, const Scalars& s,
                          int* d_err, cudaStream_t st, std::string* err,
                          cudaEvent_t* ev = nullptr);

@@ -118,6 +118,29 @@ struct GemmArgs {
   int* err;
 };
 
+// Small real instances (m, n, k <= 64) of a split plan: one fused kernel
+// (split_small.cu) reads A and B, cuts the digits into shared memory and
+// multiplies them with mma.sync. A work item is up to 16 instances of one
+// padded edge t (16, 32 or 64) that one CTA's instance groups take together.
+constexpr int kSmallMax = 64;                 // largest m, n and k of a small instance
+constexpr size_t kSmallSmemMax = 232448;      // dynamic shared memory of one CTA
+struct SmallItem {
+  int32_t first;  // position in the plan's small-instance list
+  int16_t count;  // instances (<= the groups per CTA for this t)
+  int16_t t;      // padded edge: 16, 32 or 64
+};
+struct SmallArgs {
+  const SInst* inst;
+  const int32_t* ids;  // small-instance list (instance indices)
+  const SmallItem* items;
+  int64_t nitems;
+  const double* A;
+  const double* B;
+  double* C;
+  Scalars sc;
+  int skip_product;  // alpha == 0: C = beta C
+};
+
 // ---- small device helpers --------------------------------------------------------------
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -564,6 +587,14 @@ __device__ __forceinline__ double fixed_to_double_fast(long long a, int E, bool&
       sign | ((unsigned long long)(biased & 0x7FF) << 52) | (mant & ((1ull << 52) - 1));
   return zero ? 0.0 : __longlong_as_double((long long)bits);
 }
+
+// The small-instance kernel (split_small.cu): slice counts and digit widths it
+// has compiled versions for, instances per work item, shared memory, launch.
+bool split_small_supported(int s, int beta);
+bool split_small_route(int s, int64_t m, int64_t n, int64_t k);  // instance to this kernel?
+int split_small_groups(int s, int t);  // instances per item for padded edge t
+size_t split_small_smem(int s);
+cudaError_t launch_split_small(int s, int grid, cudaStream_t st, const SmallArgs& g);
 
 // GEMM launchers, one per element type (split_gemm_r64.cu, split_gemm_c128.cu).
 cudaError_t launch_split_gemm_r64(int s, int grid, size_t smem, cudaStream_t st, const GemmArgs& g);

@@ -28,9 +28,83 @@ def test_size_mix_loguniform_reduced(gpu, s):
     b = synth.size_mix_loguniform(count=150)
     C, plan = run_grouped(b, split(s))
     info = plan.info()
-    assert info["slices"] == s and info["launches_per_call"] == 2
+    # slicer, small-instance kernel (n <= 64), tile kernel
+    assert info["slices"] == s and info["launches_per_call"] == 3
     e = errors(b, host(C), oracle_batch(b))
     assert e.max() <= TOL_SPLIT[s], (s, e.max())
+
+
+def _small_batch(seed, count, pad=True):
+    """Real instances with m, n, k in [1, 64] (k = 0 and the extremes included),
+    leading dimensions padded beyond m or k, log-uniform entries."""
+    rng = np.random.default_rng(seed)
+    shapes = [(int(rng.integers(1, 65)), int(rng.integers(1, 65)), int(rng.integers(1, 65)))
+              for _ in range(count)]
+    shapes += [(64, 64, 64), (1, 1, 1), (64, 1, 64), (1, 64, 64), (33, 17, 0), (16, 16, 16)]
+    rows, ao, bo, co = [], 0, 0, 0
+    for (m, n, k) in shapes:
+        lda = m + (int(rng.integers(0, 5)) if pad else 0)
+        ldb = max(k, 1) + (int(rng.integers(0, 5)) if pad else 0)
+        ldc = m + (int(rng.integers(0, 5)) if pad else 0)
+        rows.append((m, n, k, lda, ldb, ldc, ao, bo, co))
+        ao += lda * max(k, 1) + 8
+        bo += ldb * n + 8
+        co += ldc * n + 8
+    table = np.array(rows, dtype=np.int64)
+
+    def fill(size):
+        return rng.choice([-1.0, 1.0], size) * 10.0 ** rng.uniform(-4, 4, size)
+
+    return synth.Batch("small", "r64", table, fill(ao), fill(bo), fill(co), -1.5, 0.75)
+
+
+@pytest.mark.parametrize("s", [3, 6, 9])
+def test_small_instance_kernel(gpu, s):
+    """Real instances with m, n, k <= 64 go to the fused small-instance kernel
+    (digits cut into shared memory, level sums on mma.sync); the same batch
+    planned with BG_PLAN_SPLIT_TILES runs on the digit-plane tile kernels. Both
+    meet the mode's tolerance against the oracle."""
+    import json
+    b = _small_batch(100 + s, 300)
+    ref = oracle_batch(b)
+    C, plan = run_grouped(b, split(s))
+    d = json.loads(plan.describe())["split"]
+    # the planner's route: edges <= 32 always; 33..64 above 48 (9 slices), 40 (6), 32 (3)
+    edge = b.table[:, :3].max(axis=1)
+    small = (edge <= 32) | (edge > {9: 48, 6: 40, 3: 32}[s])
+    assert d["small_instances"] == int(small.sum()) > 0
+    assert (d["units"] == 0) == bool(small.all())
+    assert plan.info()["launches_per_call"] == (1 if small.all() else 3)
+    e = errors(b, host(C), ref)
+    assert e.max() <= TOL_SPLIT[s], (s, e.max())
+    Ct, plan_t = run_grouped(b, split(s), bg.BG_PLAN_SPLIT_TILES)
+    dt = json.loads(plan_t.describe())["split"]
+    assert dt["small_instances"] == 0 and dt["units"] > 0
+    et = errors(b, host(Ct), ref)
+    assert et.max() <= TOL_SPLIT[s], (s, et.max())
+    bg.check_device_errors()
+
+
+def test_small_instance_kernel_alpha_zero_and_nan_c(gpu):
+    """alpha = 0 reads neither A nor B (NaN there); beta = 0 does not read C (NaN there)."""
+    b = _small_batch(7, 80)
+    plan = bg.batched_gemm_plan("r64", b.table, split(9))
+    Cd = dev(b.C)
+    bg.batched_gemm_grouped(plan, dev(np.full_like(b.A, np.nan)), dev(np.full_like(b.B, np.nan)),
+                            Cd, 0.0, 2.0)
+    live = np.zeros(b.C.size, dtype=bool)  # C elements of the instances (not the ldc padding)
+    for i in range(b.count):
+        m, n, _, _, _, ldc, _, _, co = (int(v) for v in b.table[i])
+        for j in range(n):
+            live[co + j * ldc: co + j * ldc + m] = True
+    assert np.array_equal(host(Cd), np.where(live, 2.0 * b.C, b.C))
+    Cn = np.full_like(b.C, np.nan)
+    Cd = dev(Cn)
+    bg.batched_gemm_grouped(plan, dev(b.A), dev(b.B), Cd, 1.0, 0.0)
+    b0 = synth.Batch(b.name, b.dtype, b.table, b.A, b.B, np.zeros_like(b.C), 1.0, 0.0)
+    got = host(Cd)
+    e = errors(b0, got, oracle_batch(b0))
+    assert np.isfinite(e).all() and e.max() <= TOL_SPLIT[9]
 
 
 @pytest.mark.parametrize("s", [3, 6, 9])
@@ -60,8 +134,12 @@ def test_autotuned_plan_routes_and_matches_oracle(gpu, s, tmp_path):
     e = errors(b, host(C), oracle_batch(b))
     assert e.max() <= TOL_SPLIT[s], (s, e.max())
     n_split = sum(1 for v in routes.values() if v == "split")
-    want = 1 + (1 if n_split else 0) + (1 if n_split < len(routes) else 0)
-    assert plan.info()["launches_per_call"] == (want if n_split else want - 1)
+    sp = d.get("split")
+    assert (sp is not None) == (n_split > 0)
+    # split part: slicer, tile kernel, small-instance kernel (each when it has work); FP64 part
+    want = (sum(1 for key in ("slice_jobs", "units", "small_instances") if sp[key] > 0) if sp else 0)
+    want += 1 if n_split < len(routes) else 0
+    assert plan.info()["launches_per_call"] == want
     C2, plan2 = run_grouped(b, split(s), flags, cache_path=cache)
     d2 = json.loads(plan2.describe())
     assert {tuple(c["bucket"]): c["program"] for c in d2["classes"]} == routes

@@ -40,14 +40,19 @@ UNIT = "TFLOP/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one
-# ncu capture of the 2000-instance log-uniform size-mix batch, seed 3 (profiles/),
-# divided by that batch's algorithmic bytes (990601216): a full launch's traffic
-# is this ratio times its own algorithmic bytes. Valid only while the split kernel sources
-# hash to NCU_SOURCES_SHA; otherwise the traffic is reported as null.
-NCU_TRAFFIC_PER_BYTE = {"split9": {"gemm": 1.805783e9 / 990601216.0,
-                                   "slicer": 1.810911e9 / 990601216.0}}
-NCU_SOURCES = ("split.cu", "split_common.cuh", "split_gemm.cuh", "split_gemm_r64.cu")
-NCU_SOURCES_SHA = "6f32ba6f69760916"
+# single-metric ncu capture of the headline batch itself (20000-instance
+# log-uniform size mix, seed 3, 9 slices; profiles/), divided by that batch's
+# Eq. (1) bytes (10314440704): a launch's traffic is this ratio times its own
+# batch's Eq. (1) bytes (exactly the captured figure for the headline batch).
+# Valid only while the split kernel sources hash to NCU_SOURCES_SHA; otherwise
+# the traffic is reported as null.
+NCU_EQ1_BYTES = 10314440704.0
+NCU_TRAFFIC_PER_BYTE = {"split9": {"gemm": (13596686336 + 2371740928) / NCU_EQ1_BYTES,
+                                   "slicer": (7137454848 + 10727769600) / NCU_EQ1_BYTES,
+                                   "small": (560867584 + 155567104) / NCU_EQ1_BYTES}}
+NCU_SOURCES = ("split.cu", "split_common.cuh", "split_gemm.cuh", "split_gemm_r64.cu",
+               "split_small.cu")
+NCU_SOURCES_SHA = "546d4ee15b9f7b2b"
 
 
 def split_sources_sha() -> str:
@@ -1027,7 +1032,9 @@ def main():
                               "frac": sm_tf / sm_pk,
                               "peak_source": "bf16 burst / 4 (mma.sync rate, 2048 of 8192 "
                                              "flop/clk/SM)",
-                              "flops_per_launch": pairs * small_fl}
+                              "flops_per_launch": pairs * small_fl,
+                              "traffic": (NCU_TRAFFIC_PER_BYTE[m]["small"] * batch.bytes_moved()
+                                          if traffic_ok and m in NCU_TRAFFIC_PER_BYTE else None)}
             sl_ms = r["kernel_ms"][0]
             sl_bytes = (ab_elems - small_ab) * (esz + 2.0 * s * (4.0 if batch.dtype == "c128" else 1.0))
             r["slicer"] = {"kernel": "split_slice_kernel", "bound": "hbm",
@@ -1037,6 +1044,12 @@ def main():
                            "ms": sl_ms, "algorithmic_bytes": sl_bytes,
                            "traffic": (NCU_TRAFFIC_PER_BYTE[m]["slicer"] * batch.bytes_moved()
                                        if traffic_ok and m in NCU_TRAFFIC_PER_BYTE else None)}
+            if r["slicer"]["traffic"] is not None:
+                r["slicer"]["traffic_over_algorithmic"] = r["slicer"]["traffic"] / sl_bytes
+                step_traffic = (r["slicer"]["traffic"] + r["roofline"]["traffic"]
+                                + (r["small"]["traffic"] if "small" in r else 0.0))
+                r["step_traffic"] = {"bytes": step_traffic, "eq1_bytes": batch.bytes_moved(),
+                                     "over_eq1": step_traffic / batch.bytes_moved()}
             r["tensor_tflops_per_step"] = tf / (r["ms_per_step"] * 1e-3) / 1e12
         r["error"] = errs.get(m, {})
 

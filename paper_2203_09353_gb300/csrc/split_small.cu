@@ -9,9 +9,10 @@
 // Here an instance is handled by a group of warps sized to its padded edge
 // T (16, 32 or 64): (T / 16)^2 warps, each owning one 16 x 16 output block,
 // so that a CTA of 16 warps runs 16, 4 or 1 instances side by side. A group:
-//  1. loads its operands into registers (each thread: 8 values of one row of
-//     A, 8 values of one k index of B) and takes the line exponents of A's
-//     rows and B's columns;
+//  1. loads its operands into registers (each thread: four pairs of
+//     neighbouring k values, of one row of A and of four columns of B),
+//     takes the line exponents of A's rows and B's columns, and asks L2 for
+//     the operands of the CTA's next work item;
 //  2. cuts every value into its digits straight into shared memory: S planes
 //     of A (T rows x T k, BF16) and of B^T (T columns x T k), rows padded by
 //     8 values so that ldmatrix reads are free of bank conflicts, and sums
@@ -89,22 +90,22 @@ __device__ __forceinline__ int value_exponent(double x) {
 // Line exponent from the max of value exponents (0 for an all-zero line).
 __device__ __forceinline__ int line_e(int v) { return v == INT_MIN ? 0 : v; }
 
-// Digits of x at line exponent e into the planes (row `line`, column kk),
-// most significant first; returns the bound |d_1| + 0.51 of its absolute
-// digit weight.
-template <int S, int BETA, int ROWB, int PLANE>
-__device__ __forceinline__ float cut_store(double x, int e, long long bias, uint8_t* planes,
-                                           int line, int kk) {
-  uint32_t lo, hi;
-  biased_fixed<S, BETA>(x, e, bias, lo, hi);
-  const float top = top_digit<S, BETA>(lo, hi);
-  uint8_t* dst = planes + line * ROWB + kk * 2;
-  *reinterpret_cast<uint16_t*>(dst) = (uint16_t)(__float_as_uint(top) >> 16);
+// Digits of two values of one line (neighbouring k, the same line exponent e)
+// into the planes at `dst` (plane p at dst + p PLANE), one 32-bit word per
+// plane: BF16 of the first value low, of the second high. Returns the bounds
+// |d_1| + 0.51 of their absolute digit weights.
+template <int S, int BETA, int PLANE>
+__device__ __forceinline__ float2 cut_pair(double x0, double x1, int e, long long bias,
+                                           uint8_t* dst) {
+  uint32_t lo0, hi0, lo1, hi1;
+  biased_fixed<S, BETA>(x0, e, bias, lo0, hi0);
+  biased_fixed<S, BETA>(x1, e, bias, lo1, hi1);
+  const float t0 = top_digit<S, BETA>(lo0, hi0), t1 = top_digit<S, BETA>(lo1, hi1);
+  *reinterpret_cast<uint32_t*>(dst) = __byte_perm(__float_as_uint(t0), __float_as_uint(t1), 0x7632);
 #pragma unroll
   for (int p = 1; p < S; ++p)
-    *reinterpret_cast<uint16_t*>(dst + p * PLANE) =
-        (uint16_t)(lower_digit_pair<S, BETA>(p, lo, hi, lo, hi) & 0xFFFFu);
-  return fabsf(top) + 0.51f;
+    *reinterpret_cast<uint32_t*>(dst + p * PLANE) = lower_digit_pair<S, BETA>(p, lo0, hi0, lo1, hi1);
+  return make_float2(fabsf(t0) + 0.51f, fabsf(t1) + 0.51f);
 }
 
 // al^2 in units of 2^-8, rounded up (integer sums do not depend on their order)
@@ -112,14 +113,46 @@ __device__ __forceinline__ uint32_t norm_units(float al) {
   return __float2uint_ru(al * al * 256.0f * 1.0001f);
 }
 
+// L2 prefetch of the operands of the next work item's instances (those this
+// group would take: gid, gid + NG, ...), issued while the current instance's
+// loads are in flight; the instance records on the way are then in L2 too.
+template <int GT>
+__device__ __forceinline__ void prefetch_next(const SmallArgs& g, int64_t next, int gid, int ng,
+                                              int tg) {
+  if (next < 0) return;
+  const SmallItem nx = g.items[next];
+  for (int q = gid; q < nx.count; q += ng) {
+    const SInst ni = g.inst[g.ids[nx.first + q]];
+    const int ca = (ni.m + 15) >> 4, cb = (ni.k + 15) >> 4;  // 128-byte pieces per column
+    const int na = ni.k * ca, nb = ni.n * cb;
+    for (int x = tg; x < na + nb; x += GT) {
+      const double* p;
+      if (x < na) {
+        p = g.A + ni.a_off + (int64_t)(x / ca) * ni.lda + min(16 * (x % ca), ni.m - 1);
+      } else {
+        const int y = x - na;
+        p = g.B + ni.b_off + (int64_t)(y / cb) * ni.ldb + min(16 * (y % cb), ni.k - 1);
+      }
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    }
+  }
+}
+
 // One instance on one group of (T / 16)^2 warps; tg = thread within the group.
 template <int S, int BETA, int T>
 __device__ __forceinline__ void small_instance(const SmallArgs& g, const SInst& in, uint8_t* gsm,
-                                               int gid, int tg, const DigitCtx& dc) {
+                                               int gid, int tg, const DigitCtx& dc, int64_t next) {
   using SH = SmallShape<S, T>;
   constexpr int NW = SH::NW, GT = SH::GT, ROWB = SH::ROWB, PLANE = SH::PLANE;
-  constexpr int STEP = GT / T;        // line stride between a thread's 8 values (8 STEP = T)
-  constexpr int W = T < 32 ? T : 32;  // lanes of a warp that share one column of B
+  // A warp covers RW lines x KW k of A (rows) and of B^T (columns), each
+  // thread four pairs of neighbouring k: a warp's 32-bit digit stores then
+  // hit 32 distinct banks on both sides
+  constexpr int KW = T < 32 ? T : 32;  // k per warp
+  constexpr int RW = 256 / KW;         // lines per warp
+  constexpr int NRB = T / RW;          // line blocks per instance
+  constexpr int POFF = 32 / RW;        // A: lanes sharing a row, stride of a thread's pairs
+  constexpr int PL = KW / 2;           // B: lanes sharing a column
+  constexpr int CPW = 32 / PL;         // B: columns per lane set
   uint8_t* planesA = gsm;
   uint8_t* planesB = gsm + S * PLANE;
   int* eA = reinterpret_cast<int*>(gsm + 2 * S * PLANE);
@@ -135,33 +168,43 @@ __device__ __forceinline__ void small_instance(const SmallArgs& g, const SInst& 
     n2A[x] = 0;
     n2B[x] = 0;
   }
-  // ---- 1. operands into registers: A row ia at k = ka0 + STEP r; B at k = kb,
-  // column jb0 + STEP r (consecutive threads read consecutive addresses)
-  const int ia = tg % T, ka0 = tg / T;
-  const int kb = tg % T, jb0 = tg / T;
+  // ---- 1. operands into registers. A: row ia, k = ka0 + 2 POFF r (+1);
+  // B: column jb0 + CPW r, k = kb (+1). Neighbouring lanes read neighbouring
+  // addresses (A is column-major: rows; B: k).
+  const int blk = wg % NRB, kblk = wg / NRB;
+  const int ia = RW * blk + lane % RW, ka0 = KW * kblk + 2 * (lane / RW);
+  const int jb0 = RW * blk + lane / PL, kb = KW * kblk + 2 * (lane % PL);
   double va[8], vb[8];
   {
     const double* A = g.A + in.a_off;
     const double* B = g.B + in.b_off;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int kk = ka0 + STEP * r, j = jb0 + STEP * r;
-      va[r] = (prod && ia < m && kk < k) ? __ldg(A + ia + (int64_t)kk * in.lda) : 0.0;
-      vb[r] = (prod && kb < k && j < n) ? __ldg(B + kb + (int64_t)j * in.ldb) : 0.0;
+    for (int r = 0; r < 4; ++r) {
+      const int kk = ka0 + 2 * POFF * r, j = jb0 + CPW * r;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        va[2 * r + h] =
+            (prod && ia < m && kk + h < k) ? __ldg(A + ia + (int64_t)(kk + h) * in.lda) : 0.0;
+        vb[2 * r + h] =
+            (prod && kb + h < k && j < n) ? __ldg(B + kb + h + (int64_t)j * in.ldb) : 0.0;
+      }
     }
   }
+  prefetch_next<GT>(g, next, gid, SH::NG, tg);
   group_sync<NW>(gid);  // line data initialised
   {
     int ea = INT_MIN;
 #pragma unroll
     for (int r = 0; r < 8; ++r) ea = max(ea, value_exponent(va[r]));
-    if (ea != INT_MIN) atomicMax(&eA[ia], ea);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      int eb = value_exponent(vb[r]);
+    for (int o = RW; o < 32; o <<= 1) ea = max(ea, __shfl_xor_sync(0xFFFFFFFFu, ea, o));
+    if (lane < RW && ea != INT_MIN) atomicMax(&eA[ia], ea);
 #pragma unroll
-      for (int o = W / 2; o > 0; o >>= 1) eb = max(eb, __shfl_xor_sync(0xFFFFFFFFu, eb, o));
-      if (lane % W == 0 && eb != INT_MIN) atomicMax(&eB[jb0 + STEP * r], eb);
+    for (int r = 0; r < 4; ++r) {
+      int eb = max(value_exponent(vb[2 * r]), value_exponent(vb[2 * r + 1]));
+#pragma unroll
+      for (int o = PL / 2; o > 0; o >>= 1) eb = max(eb, __shfl_xor_sync(0xFFFFFFFFu, eb, o));
+      if (lane % PL == 0 && eb != INT_MIN) atomicMax(&eB[jb0 + CPW * r], eb);
     }
   }
   group_sync<NW>(gid);
@@ -171,21 +214,27 @@ __device__ __forceinline__ void small_instance(const SmallArgs& g, const SInst& 
     const int e_a = line_e(eA[ia]);
     uint32_t sa = 0;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int kk = ka0 + STEP * r;
-      const float al = cut_store<S, BETA, ROWB, PLANE>(va[r], e_a, dc.bias64, planesA, ia, kk);
-      if (ia < m && kk < k) sa += norm_units(al);
+    for (int r = 0; r < 4; ++r) {
+      const int kk = ka0 + 2 * POFF * r;
+      const float2 al = cut_pair<S, BETA, PLANE>(va[2 * r], va[2 * r + 1], e_a, dc.bias64,
+                                                 planesA + ia * ROWB + kk * 2);
+      if (ia < m && kk < k) sa += norm_units(al.x);
+      if (ia < m && kk + 1 < k) sa += norm_units(al.y);
     }
-    if (ia < m) atomicAdd(&n2A[ia], sa);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int j = jb0 + STEP * r;
-      const float al =
-          cut_store<S, BETA, ROWB, PLANE>(vb[r], line_e(eB[j]), dc.bias64, planesB, j, kb);
-      uint32_t sb = (kb < k && j < n) ? norm_units(al) : 0u;
+    for (int o = RW; o < 32; o <<= 1) sa += __shfl_xor_sync(0xFFFFFFFFu, sa, o);
+    if (lane < RW && ia < m && sa) atomicAdd(&n2A[ia], sa);
 #pragma unroll
-      for (int o = W / 2; o > 0; o >>= 1) sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
-      if (lane % W == 0 && sb) atomicAdd(&n2B[j], sb);
+    for (int r = 0; r < 4; ++r) {
+      const int j = jb0 + CPW * r;
+      const float2 al = cut_pair<S, BETA, PLANE>(vb[2 * r], vb[2 * r + 1], line_e(eB[j]),
+                                                 dc.bias64, planesB + j * ROWB + kb * 2);
+      uint32_t sb = 0;
+      if (j < n && kb < k) sb += norm_units(al.x);
+      if (j < n && kb + 1 < k) sb += norm_units(al.y);
+#pragma unroll
+      for (int o = PL / 2; o > 0; o >>= 1) sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
+      if (lane % PL == 0 && sb) atomicAdd(&n2B[j], sb);
     }
   }
   group_sync<NW>(gid);
@@ -292,7 +341,13 @@ __device__ __forceinline__ void small_instance(const SmallArgs& g, const SInst& 
       for (int c = 0; c < 2; ++c) {
         const int j = c0 + 8 * nh + 2 * tq + c;
         if (j >= n) continue;
-        const double x = prod ? fixed_to_double(accI[h][nh][c], Ebase + line_e(eB[j])) : 0.0;
+        double x = 0.0;
+        if (prod) {
+          const int E = Ebase + line_e(eB[j]);
+          bool bad = false;
+          x = fixed_to_double_fast(accI[h][nh][c], E, bad);
+          if (bad) x = fixed_to_double(accI[h][nh][c], E);
+        }
         double v = alpha_one ? x : g.sc.alpha_re * x;
         if (!g.sc.beta_zero) v = fma(g.sc.beta_re, cold[h][nh][c], v);
         Cb[i + (int64_t)j * in.ldc] = v;
@@ -301,13 +356,13 @@ __device__ __forceinline__ void small_instance(const SmallArgs& g, const SInst& 
 }
 
 template <int S, int BETA, int T>
-__device__ __forceinline__ void small_item(const SmallArgs& g, const SmallItem& item,
+__device__ __forceinline__ void small_item(const SmallArgs& g, const SmallItem& item, int64_t next,
                                            uint8_t* sm, const DigitCtx& dc) {
   using SH = SmallShape<S, T>;
   const int gid = threadIdx.x / SH::GT, tg = threadIdx.x % SH::GT;
   if (gid >= SH::NG || gid >= item.count) return;
   const SInst in = g.inst[g.ids[item.first + gid]];
-  small_instance<S, BETA, T>(g, in, sm + gid * SH::GROUP_BYTES, gid, tg, dc);
+  small_instance<S, BETA, T>(g, in, sm + gid * SH::GROUP_BYTES, gid, tg, dc, next);
 }
 
 template <int S, int BETA>
@@ -316,9 +371,10 @@ __global__ void __launch_bounds__(kSmallThreads, 1) split_small_kernel(const Sma
   const DigitCtx dc = digit_ctx<S>(BETA);
   for (int64_t it = blockIdx.x; it < g.nitems; it += gridDim.x) {
     const SmallItem item = g.items[it];
-    if (item.t == 16) small_item<S, BETA, 16>(g, item, sm, dc);
-    else if (item.t == 32) small_item<S, BETA, 32>(g, item, sm, dc);
-    else small_item<S, BETA, 64>(g, item, sm, dc);
+    const int64_t next = it + gridDim.x < g.nitems ? it + gridDim.x : -1;
+    if (item.t == 16) small_item<S, BETA, 16>(g, item, next, sm, dc);
+    else if (item.t == 32) small_item<S, BETA, 32>(g, item, next, sm, dc);
+    else small_item<S, BETA, 64>(g, item, next, sm, dc);
     __syncthreads();  // the next item may lay the shared memory out differently
   }
 }
@@ -338,12 +394,13 @@ bool split_small_supported(int s, int beta) {
 }
 
 // Which small instances the kernel takes. Edges up to 32 always (measured
-// 0.2-0.5x the time of the tile kernels on uniform batches of n = 16, 24, 32
-// at 3, 6 and 9 slices). Edges 33..64 run padded to 64 here, one instance per
-// CTA; they come here only where that measured faster than the tiles (whose
-// column width is 48 at 9 slices, 80 at 6): above 48 at 9 slices (n = 56,
-// 64: 0.73-0.75x), above 40 at 6 slices (n = 48..64: 0.63-0.72x; n = 40:
-// 1.12x), always at 3 slices (n = 40..64: 0.82-0.87x).
+// 0.21-0.49x the time of the tile kernels on uniform batches of n = 16, 24,
+// 32 at 3, 6 and 9 slices). Edges 33..64 run padded to 64 here, one instance
+// per CTA; they come here only where that measured faster than the tiles
+// (whose column width is 48 at 9 slices, 80 at 6): above 48 at 9 slices
+// (n = 56, 64: 0.67-0.69x; n = 40, 48: 1.00x), above 40 at 6 slices
+// (n = 48..64: 0.56-0.68x; n = 40: 1.00x), always at 3 slices (n = 40..64:
+// 0.76-0.79x).
 bool split_small_route(int s, int64_t m, int64_t n, int64_t k) {
   const int64_t e = m > n ? (m > k ? m : k) : (n > k ? n : k);
   if (e > kSmallMax) return false;

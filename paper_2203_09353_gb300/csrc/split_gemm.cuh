@@ -12,13 +12,16 @@ namespace splitk {
 // and column exponents are loaded first, so that all loads are in flight
 // together; the conversions are straight-line code and the rare value
 // outside the normal FP64 range is redone exactly afterwards.
-template <bool CPLX, bool FASTCONV>
+// A1: alpha == 1 (no multiply). CM: 0 = C is alpha x (C not read), 1 = alpha
+// x + beta C, 2 = alpha x + C (a later pass of a long k adds to C). Both are
+// compile-time so that no FP64 instruction runs that the case does not need:
+// on this part a warp-wide FP64 instruction holds the FP64 pipe for about 64
+// clocks, and a runtime test here compiles to the multiply plus a select.
+template <bool CPLX, bool FASTCONV, bool A1, int CM>
 __device__ __forceinline__ void epi_store8(const GemmArgs& g, const long long (&acc)[8],
                                            const int32_t* mb, int colb, bool rvalid, int cmin,
                                            int cmax, int coff, int64_t cbase, int64_t ldcv,
-                                           int Ebase, bool first_pass, bool alpha_one, int rr,
-                                           int dcol) {
-  const bool need_c = !first_pass || !g.sc.beta_zero;
+                                           int Ebase, int rr, int dcol) {
   double cv[8];
   int fj[8];
 #pragma unroll
@@ -26,7 +29,7 @@ __device__ __forceinline__ void epi_store8(const GemmArgs& g, const long long (&
     const int col = colb + j;
     const bool valid = rvalid && col >= cmin && col < cmax;
     fj[j] = __ldg(mb + col);
-    cv[j] = (valid && need_c) ? g.C[cbase + (int64_t)(col + coff) * ldcv] : 0.0;
+    cv[j] = (CM != 0 && valid) ? g.C[cbase + (int64_t)(col + coff) * ldcv] : 0.0;
   }
   double xs[8];
   if constexpr (FASTCONV) {
@@ -50,24 +53,49 @@ __device__ __forceinline__ void epi_store8(const GemmArgs& g, const long long (&
     if constexpr (!CPLX) {
       if (valid) {
         double v = x;
-        if (!alpha_one) v = g.sc.alpha_re * x;
-        if (!first_pass) v += cv[j];
-        else if (!g.sc.beta_zero) v = fma(g.sc.beta_re, cv[j], v);
+        if constexpr (!A1) v = g.sc.alpha_re * x;
+        if constexpr (CM == 2) v += cv[j];
+        if constexpr (CM == 1) v = fma(g.sc.beta_re, cv[j], v);
         *cp = v;
       }
     } else {
-      const double xp = __shfl_xor_sync(0xFFFFFFFFu, x, 1);
-      const double cpn = __shfl_xor_sync(0xFFFFFFFFu, cv[j], 1);
+      double xp = 0.0, cpn = 0.0;
+      if constexpr (!A1) xp = __shfl_xor_sync(0xFFFFFFFFu, x, 1);
+      if constexpr (CM == 1) cpn = __shfl_xor_sync(0xFFFFFFFFu, cv[j], 1);
       if (valid) {
         const double sgn = (rr & 1) ? 1.0 : -1.0;  // im row: +, re row: -
-        double v = fma(g.sc.alpha_re, x, sgn * g.sc.alpha_im * xp);
-        if (!first_pass) v += cv[j];
-        else if (!g.sc.beta_zero) v = fma(g.sc.beta_re, cv[j], fma(sgn * g.sc.beta_im, cpn, v));
+        double v = x;
+        if constexpr (!A1) v = fma(g.sc.alpha_re, x, sgn * g.sc.alpha_im * xp);
+        if constexpr (CM == 2) v += cv[j];
+        if constexpr (CM == 1) v = fma(g.sc.beta_re, cv[j], fma(sgn * g.sc.beta_im, cpn, v));
         if (col == dcol) v = 0.0;  // Hermitian update: real diagonal
         *cp = v;
       }
     }
   }
+}
+
+// epi_store8 for the warp-uniform case at hand.
+template <bool CPLX, bool FASTCONV>
+__device__ __forceinline__ void epi_store8_for(const GemmArgs& g, const long long (&acc)[8],
+                                               const int32_t* mb, int colb, bool rvalid, int cmin,
+                                               int cmax, int coff, int64_t cbase, int64_t ldcv,
+                                               int Ebase, bool first_pass, bool alpha_one, int rr,
+                                               int dcol) {
+  const int cm = first_pass ? (g.sc.beta_zero ? 0 : 1) : 2;
+#define BG_EPI(A, C)                                                                        \
+  epi_store8<CPLX, FASTCONV, A, C>(g, acc, mb, colb, rvalid, cmin, cmax, coff, cbase, ldcv, \
+                                   Ebase, rr, dcol)
+  if (alpha_one) {
+    if (cm == 0) BG_EPI(true, 0);
+    else if (cm == 1) BG_EPI(true, 1);
+    else BG_EPI(true, 2);
+  } else {
+    if (cm == 0) BG_EPI(false, 0);
+    else if (cm == 1) BG_EPI(false, 1);
+    else BG_EPI(false, 2);
+  }
+#undef BG_EPI
 }
 
 // SF > 0: the slice count is the compile-time constant SF (the MMA issue loop
@@ -396,7 +424,7 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
                 }
               }
             }
-            epi_store8<CPLX, kFastConv>(g, acc, mb, col0 + j0, rvalid, cmin, cmax, coff, cbase, ldcv, Ebase,
+            epi_store8_for<CPLX, kFastConv>(g, acc, mb, col0 + j0, rvalid, cmin, cmax, coff, cbase, ldcv, Ebase,
                              c == 0, alpha_one, rr, dcol);
           }
           if (npass > 0) {
@@ -461,7 +489,7 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
           }
           // ---- exact conversion, alpha/beta, store (TMEM already free: overlaps the next MMAs).
           for (int j0 = 0; j0 < COLS; j0 += 8) {
-            epi_store8<CPLX, kFastConv>(g, *reinterpret_cast<const long long(*)[8]>(acc), mb, col0 + j0,
+            epi_store8_for<CPLX, kFastConv>(g, *reinterpret_cast<const long long(*)[8]>(acc), mb, col0 + j0,
                              rvalid, cmin, cmax, coff, cbase, ldcv, Ebase, c == 0, alpha_one, rr, dcol);
             // rotate the next 8 accumulators into place (keeps the loop body small)
 #pragma unroll

@@ -138,6 +138,33 @@ __device__ __forceinline__ void prefetch_next(const SmallArgs& g, int64_t next, 
   }
 }
 
+// alpha and beta of Eq. (1) and the store of a thread's outputs. A1: alpha ==
+// 1, BZ: beta == 0, both compile-time so that no FP64 instruction runs that
+// the case does not need (a runtime test compiles to the multiply and a
+// select; on this part a warp-wide FP64 instruction holds the FP64 pipe for
+// about 64 clocks).
+template <bool A1, bool BZ>
+__device__ __forceinline__ void small_store(const SmallArgs& g, const double (&xs)[2][2][2],
+                                            const double (&cold)[2][2][2], double* Cb, int64_t ldc,
+                                            const int (&rows)[2], int m, int n, int c0, int tq) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = rows[h];
+    if (i >= m) continue;
+#pragma unroll
+    for (int nh = 0; nh < 2; ++nh)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int j = c0 + 8 * nh + 2 * tq + c;
+        if (j >= n) continue;
+        double v = xs[h][nh][c];
+        if constexpr (!A1) v = g.sc.alpha_re * v;
+        if constexpr (!BZ) v = fma(g.sc.beta_re, cold[h][nh][c], v);
+        Cb[i + (int64_t)j * ldc] = v;
+      }
+  }
+}
+
 // One instance on one group of (T / 16)^2 warps; tg = thread within the group.
 template <int S, int BETA, int T>
 __device__ __forceinline__ void small_instance(const SmallArgs& g, const SInst& in, uint8_t* gsm,
@@ -328,30 +355,33 @@ __device__ __forceinline__ void small_instance(const SmallArgs& g, const SInst& 
       }
     }
   }
-  // ---- 4. exact conversion, alpha and beta, store
-  const bool alpha_one = g.sc.alpha_re == 1.0;
+  // ---- 4. exact conversion, then alpha and beta, store
+  double xs[2][2][2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const int i = rows[h];
-    if (i >= m) continue;
+    const int i = min(rows[h], T - 1);
     const int Ebase = F[h] - 62 + line_e(eA[i]) - 2 * BETA;
 #pragma unroll
     for (int nh = 0; nh < 2; ++nh)
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const int j = c0 + 8 * nh + 2 * tq + c;
-        if (j >= n) continue;
-        double x = 0.0;
+        const int j = min(c0 + 8 * nh + 2 * tq + c, T - 1);
+        xs[h][nh][c] = 0.0;
         if (prod) {
           const int E = Ebase + line_e(eB[j]);
           bool bad = false;
-          x = fixed_to_double_fast(accI[h][nh][c], E, bad);
-          if (bad) x = fixed_to_double(accI[h][nh][c], E);
+          xs[h][nh][c] = fixed_to_double_fast(accI[h][nh][c], E, bad);
+          if (bad) xs[h][nh][c] = fixed_to_double(accI[h][nh][c], E);
         }
-        double v = alpha_one ? x : g.sc.alpha_re * x;
-        if (!g.sc.beta_zero) v = fma(g.sc.beta_re, cold[h][nh][c], v);
-        Cb[i + (int64_t)j * in.ldc] = v;
       }
+  }
+  const bool alpha_one = g.sc.alpha_re == 1.0;
+  if (alpha_one) {
+    if (g.sc.beta_zero) small_store<true, true>(g, xs, cold, Cb, in.ldc, rows, m, n, c0, tq);
+    else small_store<true, false>(g, xs, cold, Cb, in.ldc, rows, m, n, c0, tq);
+  } else {
+    if (g.sc.beta_zero) small_store<false, true>(g, xs, cold, Cb, in.ldc, rows, m, n, c0, tq);
+    else small_store<false, false>(g, xs, cold, Cb, in.ldc, rows, m, n, c0, tq);
   }
 }
 

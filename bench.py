@@ -47,12 +47,12 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # Valid only while the split kernel sources hash to NCU_SOURCES_SHA; otherwise
 # the traffic is reported as null.
 NCU_EQ1_BYTES = 10314440704.0
-NCU_TRAFFIC_PER_BYTE = {"split9": {"gemm": (13596686336 + 2371740928) / NCU_EQ1_BYTES,
-                                   "slicer": (7137454848 + 10727769600) / NCU_EQ1_BYTES,
-                                   "small": (560867584 + 155567104) / NCU_EQ1_BYTES}}
+NCU_TRAFFIC_PER_BYTE = {"split9": {"gemm": (13591069184 + 2376404224) / NCU_EQ1_BYTES,
+                                   "slicer": (7144226048 + 10727361024) / NCU_EQ1_BYTES,
+                                   "small": (560800000 + 155933440) / NCU_EQ1_BYTES}}
 NCU_SOURCES = ("split.cu", "split_common.cuh", "split_gemm.cuh", "split_gemm_r64.cu",
                "split_small.cu")
-NCU_SOURCES_SHA = "546d4ee15b9f7b2b"
+NCU_SOURCES_SHA = "0341875da8cf6794"
 
 
 def split_sources_sha() -> str:

@@ -85,6 +85,51 @@ def test_small_instance_kernel(gpu, s):
     bg.check_device_errors()
 
 
+@pytest.mark.parametrize("s", [3, 6, 9])
+def test_small_instance_kernel_extreme_exponents(gpu, s):
+    """The small-instance kernel's own line exponents and digit cut at both ends
+    of the FP64 range (every edge <= 32, so every instance takes that kernel):
+    A or B made only of subnormal values, near-overflow operands, and zero or
+    subnormal rows beside normal ones. Errors in exactly rescaled norms, as in
+    test_split_extreme_exponents."""
+    import json
+    rng = np.random.default_rng(33 + s)
+    cases = [((24, 20, 30), -1060, 1000), ((17, 31, 32), -1072, 1010),
+             ((24, 20, 30), 900, 100), ((20, 24, 30), 1000, -1050), ((32, 32, 32), 0, 0),
+             ((16, 16, 16), -1074 + 60, 0), ((9, 5, 3), 0, 0)]
+    table, la, lb, lc = synth.pack_table([c[0] for c in cases])
+    A, B, C = np.zeros(la), np.zeros(lb), np.zeros(lc)
+
+    def fill(shape, scale):
+        x = rng.uniform(-1, 1, shape)
+        return x * 2.0 ** scale if abs(scale) < 1000 else x * 2.0 ** (scale // 2) * 2.0 ** (scale - scale // 2)
+
+    for i, ((m, n, k), sa, sb) in enumerate(cases):
+        _, _, _, lda, ldb, ldc, ao, bo, co = (int(v) for v in table[i])
+        a, b = fill((m, k), sa), fill((k, n), sb)
+        if i == 4:
+            a[3, :] = 0.0                       # a zero row
+            a[5, :] = fill(k, -1074 + 8)        # a row of tiny subnormals among normal ones
+            a[7, 2] = 5e-324                    # the smallest subnormal in a normal row
+            b[:, 6] = 0.0                       # a zero column
+        A[ao:ao + lda * k] = np.asfortranarray(a).ravel(order="F")
+        B[bo:bo + ldb * n] = np.asfortranarray(b).ravel(order="F")
+    batch = synth.Batch("extreme_small", "r64", table, A, B, C, 1.0, 0.0)
+    ref = oracle_batch(batch)
+    got, plan = run_grouped(batch, split(s))
+    assert json.loads(plan.describe())["split"]["small_instances"] == len(cases)
+    got = host(got)
+    for i, ((m, n, k), sa, sb) in enumerate(cases):
+        _, _, _, lda, ldb, ldc, ao, bo, co = (int(v) for v in table[i])
+        g = got[co:co + ldc * n].reshape(n, ldc).T[:m, :]
+        r = ref[co:co + ldc * n].reshape(n, ldc).T[:m, :]
+        assert np.all(np.isfinite(g)), i
+        num = np.linalg.norm(np.ldexp(np.abs(g - r), -(sa + sb)))
+        a = np.ldexp(np.abs(batch.instance(i, "A")), -sa)
+        b = np.ldexp(np.abs(batch.instance(i, "B")), -sb)
+        assert num <= TOL_SPLIT[s] * np.linalg.norm(a) * np.linalg.norm(b), (i, num)
+
+
 def test_small_instance_kernel_alpha_zero_and_nan_c(gpu):
     """alpha = 0 reads neither A nor B (NaN there); beta = 0 does not read C (NaN there)."""
     b = _small_batch(7, 80)

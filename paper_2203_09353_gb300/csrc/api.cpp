@@ -267,10 +267,11 @@ bg_status upload(T** dptr, const std::vector<T>& v, int64_t* ws_bytes) {
 double item_cost(const WorkItem& w, const std::vector<int64_t>& mnk_k,
                  const std::vector<int64_t>& mnk_mn, const std::vector<int32_t>& order) {
   if (prog_is_small(w.prog)) {
+    const double lanes = 32.0 * (w.r0 > 0 ? w.r0 : 1);  // threads per instance
     double c = 0;
     for (int i = 0; i < w.count; ++i) {
       const int64_t id = order[w.inst + i];
-      c = std::max(c, std::ceil(mnk_mn[id] / 32.0) * (double)mnk_k[id]);
+      c = std::max(c, std::ceil(mnk_mn[id] / lanes) * (double)mnk_k[id]);
     }
     return c;
   }
@@ -281,11 +282,12 @@ double item_cost(const WorkItem& w, const std::vector<int64_t>& mnk_k,
 
 // Build the FP64 work list for instances with the given program per instance.
 // `ids` are instance (or walker) ids, `sizes` their (m, n, k), `prog_of` the
-// chosen program. Small-program instances are grouped kSmallPerCta at a time
-// in `order`; items are sorted longest first.
+// chosen program. Small-program instances are grouped in `order`, 8 to a CTA,
+// or fewer (with several warps each) when there are too few of them to give
+// each of the `grid` CTAs an item; items are sorted longest first.
 void build_items(const std::vector<int64_t>& ids, const std::vector<std::array<int64_t, 3>>& mnk,
                  const std::vector<int>& prog_of, std::vector<WorkItem>* items,
-                 std::vector<int32_t>* order, bool herk) {
+                 std::vector<int32_t>* order, bool herk, int64_t grid) {
   items->clear();
   order->clear();
   const size_t N = mnk.size();
@@ -322,12 +324,14 @@ void build_items(const std::vector<int64_t>& ids, const std::vector<std::array<i
     std::stable_sort(v.begin(), v.end(), [&](int64_t a, int64_t b) {
       return std::ceil(mn[a] / 32.0) * kk[a] > std::ceil(mn[b] / 32.0) * kk[b];
     });
-    for (size_t s = 0; s < v.size(); s += kSmallPerCta) {
+    const int g = kv.first == PROG_R64_SMALL ? small_group((int64_t)v.size(), grid) : kSmallPerCta;
+    for (size_t s = 0; s < v.size(); s += g) {
       WorkItem w;
       w.inst = (int32_t)order->size();
       w.prog = (int16_t)kv.first;
-      w.count = (int16_t)std::min<size_t>(kSmallPerCta, v.size() - s);
-      w.r0 = w.c0 = 0;
+      w.count = (int16_t)std::min<size_t>(g, v.size() - s);
+      w.r0 = kSmallPerCta / g;  // warps per instance
+      w.c0 = 0;
       for (int i = 0; i < w.count; ++i) order->push_back((int32_t)v[s + i]);
       items->push_back(w);
     }
@@ -454,7 +458,7 @@ bg_status time_class_fp64(bg_plan* p, int cls, int prog, cudaStream_t st, double
   }
   std::vector<WorkItem> items;
   std::vector<int32_t> order;
-  build_items(sids, smnk, sprog, &items, &order, false);
+  build_items(sids, smnk, sprog, &items, &order, false, p->grid);
   void *A = nullptr, *B = nullptr, *C = nullptr;
   int64_t* dt = nullptr;
   int32_t* dord = nullptr;
@@ -699,7 +703,7 @@ bg_status build_fp64_schedule(bg_plan* p, const char* cache_path, cudaStream_t s
     if (p->table[i].m > 0 && p->table[i].n > 0 && prog_of[i] != PROG_SPLIT) live.push_back(i);
   std::vector<WorkItem> items;
   std::vector<int32_t> order;
-  build_items(live, mnk, prog_of, &items, &order, (p->flags & BG_PLAN_HERK) != 0);
+  build_items(live, mnk, prog_of, &items, &order, (p->flags & BG_PLAN_HERK) != 0, p->grid);
   p->n_items = (int64_t)items.size();
   bg_status s;
   if ((s = upload(&p->d_order, order, &p->workspace_bytes)) != BG_OK) return s;

@@ -16,7 +16,7 @@ namespace bg {
 // Tile programs of the FP64 path. A work item names one program and the part
 // of the batch it covers.
 enum Prog : int16_t {
-  PROG_R64_SMALL = 0,   // one warp per instance, up to 8 instances per CTA
+  PROG_R64_SMALL = 0,   // a warp per instance (8 per CTA), or 8 warps on one instance
   PROG_R64_TILE = 1,    // 64x64 output tile, DFMA, 4x4 outputs per thread
   PROG_R64_DMMA = 2,    // 64x64 output tile, FP64 tensor-core mma.sync m8n8k4
   PROG_C128_SMALL = 3,  // one warp per complex instance
@@ -38,6 +38,13 @@ struct WorkItem {
 static_assert(sizeof(WorkItem) == 16, "WorkItem must stay 16 bytes");
 
 constexpr int kSmallPerCta = 8;   // warps (instances) per CTA in the small programs
+// Real small-program work items hold g instances that the CTA's 8 warps
+// share: g = 8 (a warp each), or g = 1 (all 8 warps on one instance) for
+// batches too small to give every resident CTA an item of 8; WorkItem.r0
+// carries the warps per instance (0 reads as 1).
+inline int small_group(int64_t instances, int64_t grid) {
+  return (instances + kSmallPerCta - 1) / kSmallPerCta >= grid ? kSmallPerCta : 1;
+}
 constexpr int kFp64Threads = 256;
 
 struct Scalars {

@@ -130,15 +130,17 @@ struct ChainSrc {
 struct FixedSched {
   int prog;
   int tm, tn;
+  int g;  // small programs: instances per item
   int64_t tiles_m, tiles_n, batch;
   __device__ WorkItem get(int64_t it) const {
     WorkItem w;
     w.prog = (int16_t)prog;
     if (tm == 0) {
-      w.inst = (int32_t)(it * kSmallPerCta);
-      const int64_t left = batch - it * kSmallPerCta;
-      w.count = (int16_t)(left < kSmallPerCta ? left : kSmallPerCta);
-      w.r0 = w.c0 = 0;
+      w.inst = (int32_t)(it * g);
+      const int64_t left = batch - it * g;
+      w.count = (int16_t)(left < g ? left : g);
+      w.r0 = kSmallPerCta / g;  // warps per instance
+      w.c0 = 0;
     } else {
       const int64_t per = tiles_m * tiles_n;
       w.inst = (int32_t)(it / per);
@@ -425,22 +427,24 @@ __device__ __forceinline__ void tile_c128(const Desc& d, int r0, int c0, const S
   }
 }
 
-// ---- small programs: one warp per instance ---------------------------------------
-// Lane l owns outputs o = l + 32 j (j < MAXOUT) of the m*n outputs in
-// column-major order, i.e. (r, c) = (o mod m, o div m). When m divides 32 the
-// row is the same for every j and the column steps by 32/m, so one A load
-// feeds MAXOUT DFMAs; otherwise every output loads its own A element.
+// ---- small programs: W warps per instance (real), one warp (complex) ----------
+// Thread t (0 <= t < 32 W) of an instance owns outputs o = t + 32 W j
+// (j < MAXOUT) of the m*n outputs in column-major order, i.e. (r, c) =
+// (o mod m, o div m). When m divides 32 the row is the same for every j and
+// the column steps by 32 W / m, so one A load feeds MAXOUT DFMAs; otherwise
+// every output loads its own A element.
 
-template <int MAXOUT>
-__device__ __forceinline__ void small_r64(const Desc& d, const Scalars& s) {
-  const int lane = threadIdx.x & 31;
+template <int MAXOUT, int W>
+__device__ __forceinline__ void small_r64(const Desc& d, const Scalars& s, int t) {
+  const int lane = t;  // thread of the instance
+  constexpr int stride = 32 * W;
   const int m = d.m, n = d.n, mn = m * n;
   const int K = s.alpha_zero ? 0 : d.k;
   double acc[MAXOUT];
 #pragma unroll
   for (int j = 0; j < MAXOUT; ++j) acc[j] = 0.0;
   if (m > 0 && (32 % m) == 0) {
-    const int r = lane % m, c0 = lane / m, cstep = 32 / m;
+    const int r = lane % m, c0 = lane / m, cstep = stride / m;
     const double* ap = d.A + r;
     const double* bp = d.B + (int64_t)c0 * d.ldb;
     const int64_t bstep = (int64_t)cstep * d.ldb;
@@ -465,7 +469,7 @@ __device__ __forceinline__ void small_r64(const Desc& d, const Scalars& s) {
     for (int p = 0; p < K; ++p) {
 #pragma unroll
       for (int j = 0; j < MAXOUT; ++j) {
-        const int o = lane + 32 * j;
+        const int o = lane + stride * j;
         if (o < mn) {
           const int r = o % m, c = o / m;
           acc[j] = fma(__ldg(d.A + r + (int64_t)p * d.lda), ld_b(d, p, c), acc[j]);
@@ -474,7 +478,7 @@ __device__ __forceinline__ void small_r64(const Desc& d, const Scalars& s) {
     }
 #pragma unroll
     for (int j = 0; j < MAXOUT; ++j) {
-      const int o = lane + 32 * j;
+      const int o = lane + stride * j;
       if (o < mn) {
         const int r = o % m, c = o / m;
         if (!keep_out(d, r, c)) continue;
@@ -573,13 +577,19 @@ __global__ void __launch_bounds__(kFp64Threads, 1)
       case PROG_C128_TILE:
         tile_c128(src.desc(w.inst), w.r0, w.c0, s, sm.c);
         break;
-      case PROG_R64_SMALL:
-        if (warp < w.count) {
-          const Desc d = src.desc(src.small_inst((int64_t)w.inst + warp));
-          if (d.m > 0 && (32 % d.m) == 0) small_r64<32>(d, s);
-          else small_r64<16>(d, s);
+      case PROG_R64_SMALL: {
+        const int W = w.r0 > 0 ? w.r0 : 1;  // warps per instance
+        const int slot = warp / W;
+        if (slot < w.count) {
+          const Desc d = src.desc(src.small_inst((int64_t)w.inst + slot));
+          const int t = (warp - slot * W) * 32 + (threadIdx.x & 31);
+          const bool fast = d.m > 0 && (32 % d.m) == 0;
+          // outputs per thread: at most 1024 (fast) or 512 (other shapes) per instance
+          if (W == 1) fast ? small_r64<32, 1>(d, s, t) : small_r64<16, 1>(d, s, t);
+          else fast ? small_r64<4, 8>(d, s, t) : small_r64<2, 8>(d, s, t);
         }
         break;
+      }
       case PROG_C128_SMALL:
         if (warp < w.count) {
           const Desc d = src.desc(src.small_inst((int64_t)w.inst + warp));
@@ -662,17 +672,20 @@ cudaError_t launch_fp64_fixed(bg_dtype dt, int prog, int64_t m, int64_t n, int64
   prog_tile(prog, &sched.tm, &sched.tn);
   sched.batch = batch;
   int64_t n_items;
+  int64_t grid = (int64_t)sm_count() * fp64_blocks_per_sm(dt);
+  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
+  sched.g = kSmallPerCta;
   if (sched.tm == 0) {
+    // the real small program spreads small batches over more CTAs
+    if (prog == PROG_R64_SMALL) sched.g = small_group(batch, grid);
     sched.tiles_m = sched.tiles_n = 1;
-    n_items = (batch + kSmallPerCta - 1) / kSmallPerCta;
+    n_items = (batch + sched.g - 1) / sched.g;
   } else {
     sched.tiles_m = (m + sched.tm - 1) / sched.tm;
     sched.tiles_n = (n + sched.tn - 1) / sched.tn;
     n_items = batch * sched.tiles_m * sched.tiles_n;
   }
   if (n_items <= 0) return cudaSuccess;
-  int64_t grid = (int64_t)sm_count() * fp64_blocks_per_sm(dt);
-  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
   if (grid > n_items) grid = n_items;
   fp64_persistent<FixedSrc, FixedSched><<<(unsigned)grid, kFp64Threads, 0, st>>>(src, sched,
                                                                                  n_items, s);

@@ -206,18 +206,47 @@ __global__ void __launch_bounds__(WARPS * 32) tridiag_kernel(double2* G, int n, 
   }
 }
 
+// 1/q for a normal q: the hardware's approximate reciprocal, then two
+// Newton-Raphson steps r <- r + r (1 - q r), each of which squares the
+// relative error (to well below 2^-80, so r is within an ulp or so of 1/q).
+// On this part an FP64 instruction is slow; this takes five of them where
+// an IEEE division takes about twice as many.
+__device__ __forceinline__ double recip_nr(double q) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(q));
+  double e = fma(-q, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-q, r, 1.0);
+  return fma(r, e, r);
+}
+
 // Number of eigenvalues of the symmetric tridiagonal (d, e2 = e^2) below x:
 // the negative pivots of T - x I (a pivot smaller than pivmin in magnitude
-// is replaced by -pivmin, as in LAPACK's dstebz).
+// is replaced by -pivmin, as in LAPACK's dstebz). The pivot recurrence
+// q_i = (d_i - x) - e2_{i-1} / q_{i-1} is backward stable: the count is exact
+// for entries perturbed by a few ulps, which also covers a quotient formed
+// with a reciprocal that is not correctly rounded. The sign and the pivmin
+// test read the bit pattern (integer compares of |q|'s bits order like the
+// magnitudes), so that they stay off the FP64 pipe.
 __device__ __forceinline__ int sturm_count(const double* d, const double* e2, int n, double x,
                                            double pivmin) {
+  const long long pmin_bits = __double_as_longlong(pivmin);
+  const double neg_pmin = -pivmin;
   double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  int cnt = q < 0.0;
+  long long qb = __double_as_longlong(q);
+  if ((qb & 0x7FFFFFFFFFFFFFFFll) < pmin_bits) {
+    q = neg_pmin;
+    qb = __double_as_longlong(q);
+  }
+  int cnt = (int)((unsigned long long)qb >> 63);
   for (int i = 1; i < n; ++i) {
-    q = (d[i] - x) - e2[i - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += q < 0.0;
+    q = fma(-e2[i - 1], recip_nr(q), d[i] - x);
+    qb = __double_as_longlong(q);
+    if ((qb & 0x7FFFFFFFFFFFFFFFll) < pmin_bits) {
+      q = neg_pmin;
+      qb = __double_as_longlong(q);
+    }
+    cnt += (int)((unsigned long long)qb >> 63);
   }
   return cnt;
 }

@@ -118,6 +118,14 @@ def test_random_states_match_oracle(gpu, S, mode):
         n2 = float(np.vdot(states[w], states[w]).real)
         assert abs(eig[w].sum() - n2) <= 1e-12 * n2
         assert np.all(np.diff(eig[w]) >= 0) and eig[w][0] >= -1e-12 * n2
+        # each eigenvalue against a library eigensolver on the same Gram matrix
+        # (the K x M column-major view X of the state, G = X X^H): Householder
+        # reduction and bisection in FP64 stay within a small multiple of
+        # n u ||G||
+        K = 1 << (S // 2)
+        X = states[w].reshape(-1, K).T
+        lam = np.linalg.eigvalsh(X @ X.conj().T)
+        assert np.max(np.abs(eig[w] - lam)) <= 1e-12 * lam[-1], (w, np.max(np.abs(eig[w] - lam)))
 
 
 def test_padded_stride_and_many_walkers(gpu):

@@ -102,9 +102,10 @@ typedef struct bg_plan bg_plan;
 /* Plan flags. */
 enum {
   BG_PLAN_AUTOTUNE = 1u,      /* time candidates per size class and keep the fastest: the FP64
-                                 tile programs; in split mode also the split path, each class
-                                 then computed by the split or the FP64 path, whichever is
-                                 faster (the FP64 path is never less accurate) */
+                                 tile programs; in split mode also the split path (for real
+                                 classes up to 64 on a side: on the small-instance kernel and
+                                 on the tile kernels, separately), each class then computed by
+                                 the fastest (the FP64 path is never less accurate) */
   BG_PLAN_USE_CACHE = 2u,     /* read/write autotune results in the JSON file cache_path */
   BG_PLAN_CAPTURE_GRAPH = 4u, /* batched_gemm_grouped replays a captured CUDA graph */
   BG_PLAN_PROFILE = 8u,       /* record CUDA events around each kernel (bg_plan_kernel_times) */

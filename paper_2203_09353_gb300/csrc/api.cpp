@@ -185,9 +185,22 @@ struct ClassInfo {
   std::vector<std::pair<int, double>> tried;
 };
 
-// Route of a class that the split path computes (ClassInfo::prog, and the
-// autotune cache's "prog" entry for split-mode keys).
+// Routes of a class that the split path computes (ClassInfo::prog, and the
+// autotune cache's "prog" entry for split-mode keys): the default rule for
+// the small-instance kernel, or (autotuned) the small-instance kernel for
+// every member it can take, or the tile kernels only.
 constexpr int PROG_SPLIT = -2;
+constexpr int PROG_SPLIT_TILES = -3;
+constexpr int PROG_SPLIT_SMALL = -4;
+inline bool is_split_route(int prog) {
+  return prog == PROG_SPLIT || prog == PROG_SPLIT_TILES || prog == PROG_SPLIT_SMALL;
+}
+inline int8_t split_route_of(int prog) {
+  return prog == PROG_SPLIT_SMALL ? 1 : prog == PROG_SPLIT_TILES ? 2 : 0;
+}
+inline const char* split_route_name(int prog) {
+  return prog == PROG_SPLIT_SMALL ? "split_small" : prog == PROG_SPLIT_TILES ? "split_tiles" : "split";
+}
 
 struct bg_plan {
   int device = 0;
@@ -382,7 +395,7 @@ std::map<std::string, int> read_cache(const char* path) {
     const char* pp = strstr(q2, "\"prog\":");
     if (!pp) continue;
     int prog = -1;
-    if (sscanf(pp + 7, "%d", &prog) == 1 && ((prog >= 0 && prog < PROG_COUNT) || prog == PROG_SPLIT))
+    if (sscanf(pp + 7, "%d", &prog) == 1 && ((prog >= 0 && prog < PROG_COUNT) || is_split_route(prog)))
       out[key] = prog;
   }
   fclose(f);
@@ -546,7 +559,7 @@ void destroy_plan(bg_plan* p) {
 // Times the split path (slicer and tensor-core GEMM) on a compact zeroed sample
 // of one class (at most about 64 MiB per operand), scaled to the whole class
 // by flops. Returns ms (median of 3 runs after one warm-up).
-bg_status time_class_split(bg_plan* p, int cls, cudaStream_t st, double* ms) {
+bg_status time_class_split(bg_plan* p, int cls, cudaStream_t st, double* ms, int8_t route) {
   const int64_t esz = p->dtype == BG_C128 ? 16 : 8;
   const bool herk = (p->flags & BG_PLAN_HERK) != 0;
   std::vector<bg_instance> sub;
@@ -573,8 +586,9 @@ bg_status time_class_split(bg_plan* p, int cls, cudaStream_t st, double* ms) {
   bg_status rs = get_ctx(&ctx);
   if (rs != BG_OK) return rs;
   SplitPlan* sp = nullptr;
+  const std::vector<int8_t> routes(sub.size(), route);
   rs = split_plan_create(&sp, p->dtype, p->prec, sub, nullptr, ctx->sms, false, st,
-                         &g_last_error, herk, (p->flags & BG_PLAN_SPLIT_TILES) == 0);
+                         &g_last_error, herk, (p->flags & BG_PLAN_SPLIT_TILES) == 0, &routes);
   if (rs != BG_OK) return rs;
   void *A = nullptr, *B = nullptr, *C = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -657,7 +671,7 @@ bg_status build_fp64_schedule(bg_plan* p, const char* cache_path, cudaStream_t s
     const std::string key = class_key(p->dtype, p->prec, ci);
     if (use_cache && cache.count(key) &&
         (std::find(cand.begin(), cand.end(), cache[key]) != cand.end() ||
-         (split && cache[key] == PROG_SPLIT))) {
+         (split && is_split_route(cache[key])))) {
       ci.prog = cache[key];
       continue;
     }
@@ -675,13 +689,24 @@ bg_status build_fp64_schedule(bg_plan* p, const char* cache_path, cudaStream_t s
         }
       }
       if (split) {
-        double ms = 0;
-        bg_status s = time_class_split(p, (int)c, st, &ms);
-        if (s != BG_OK) return s;
-        ci.tried.push_back({PROG_SPLIT, ms});
-        if (ms <= best) {
-          ci.prog = PROG_SPLIT;
-          ci.ms = ms;
+        // classes the small-instance kernel can take (real, m, n, k <= 64)
+        // are timed on it and on the tile kernels; others on the split path
+        const int beta = p->prec.beta_bits ? p->prec.beta_bits : split_default_beta(p->prec.slices);
+        const bool two = p->dtype == BG_R64 && !(p->flags & BG_PLAN_HERK) &&
+                         !(p->flags & BG_PLAN_SPLIT_TILES) &&
+                         splitk::split_small_supported(p->prec.slices, beta) && ci.key_m <= 64 &&
+                         ci.key_n <= 64 && ci.key_k <= 64;
+        const int routes[2] = {two ? PROG_SPLIT_SMALL : PROG_SPLIT, PROG_SPLIT_TILES};
+        for (int r = 0; r < (two ? 2 : 1); ++r) {
+          double ms = 0;
+          bg_status s = time_class_split(p, (int)c, st, &ms, split_route_of(routes[r]));
+          if (s != BG_OK) return s;
+          ci.tried.push_back({routes[r], ms});
+          if (ms <= best) {
+            best = ms;
+            ci.prog = routes[r];
+            ci.ms = ms;
+          }
         }
       }
       new_entries[key] = {ci.prog, ci.ms};
@@ -700,7 +725,7 @@ bg_status build_fp64_schedule(bg_plan* p, const char* cache_path, cudaStream_t s
   }
   std::vector<int64_t> live;
   for (int64_t i = 0; i < p->count; ++i)
-    if (p->table[i].m > 0 && p->table[i].n > 0 && prog_of[i] != PROG_SPLIT) live.push_back(i);
+    if (p->table[i].m > 0 && p->table[i].n > 0 && !is_split_route(prog_of[i])) live.push_back(i);
   std::vector<WorkItem> items;
   std::vector<int32_t> order;
   build_items(live, mnk, prog_of, &items, &order, (p->flags & BG_PLAN_HERK) != 0, p->grid);
@@ -890,11 +915,17 @@ bg_status batched_gemm_plan(bg_plan** out, bg_dtype dtype, int64_t count,
       return s;
     }
     std::vector<bg_instance> sub;
-    for (int64_t i = 0; i < count; ++i)
-      if (p->classes[p->inst_class[i]].prog == PROG_SPLIT) sub.push_back(p->table[i]);
+    std::vector<int8_t> routes;
+    for (int64_t i = 0; i < count; ++i) {
+      const int prog = p->classes[p->inst_class[i]].prog;
+      if (is_split_route(prog)) {
+        sub.push_back(p->table[i]);
+        routes.push_back(split_route_of(prog));
+      }
+    }
     if (!sub.empty()) {
       s = split_plan_create(&p->split, dtype, pr, sub, nullptr, ctx->sms, false, st,
-                            &g_last_error, herk, (flags & BG_PLAN_SPLIT_TILES) == 0);
+                            &g_last_error, herk, (flags & BG_PLAN_SPLIT_TILES) == 0, &routes);
       if (s != BG_OK) {
         destroy_plan(p);
         return s;
@@ -1230,12 +1261,13 @@ bg_status bg_plan_describe(const bg_plan* p, char* buf, size_t len, size_t* need
              "\"program\": \"%s\", \"timed_ms\": %.6f, \"tried\": [",
              c ? ", " : "", (long long)ci.key_m, (long long)ci.key_n, (long long)ci.key_k,
              (long long)ci.members, ci.flops * 1e-9,
-             (ci.prog >= 0 && ci.prog < PROG_COUNT) ? names[ci.prog] : "split", ci.ms);
+             (ci.prog >= 0 && ci.prog < PROG_COUNT) ? names[ci.prog] : split_route_name(ci.prog),
+             ci.ms);
     s += tmp;
     for (size_t t = 0; t < ci.tried.size(); ++t) {
       const int q = ci.tried[t].first;
       snprintf(tmp, sizeof tmp, "%s{\"program\": \"%s\", \"ms\": %.6f}", t ? ", " : "",
-               (q >= 0 && q < PROG_COUNT) ? names[q] : "split", ci.tried[t].second);
+               (q >= 0 && q < PROG_COUNT) ? names[q] : split_route_name(q), ci.tried[t].second);
       s += tmp;
     }
     s += "]}";

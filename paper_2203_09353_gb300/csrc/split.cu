@@ -446,6 +446,7 @@ struct SplitPlan {
   bool chain = false;
   bool herk = false;       // Hermitian rank-k updates (B = A^H, lower triangle)
   bool small_ok = false;   // real instances with m, n, k <= 64 go to the small-instance kernel
+  std::vector<int8_t> route;  // per instance: 0 rule, 1 small where possible, 2 tiles (may be empty)
   int sms = 0;
   int64_t count = 0;
   // device
@@ -611,7 +612,10 @@ static void make_tables(const SplitPlan* p, const std::vector<bg_instance>& tabl
   for (size_t i = 0; i < table.size(); ++i) {
     const bg_instance& t = table[i];
     if (t.m == 0 || t.n == 0) continue;
-    if (p->small_ok && !cplx && !p->herk && split_small_route(s, t.m, t.n, t.k)) {
+    const int8_t r = p->route.empty() ? 0 : p->route[i];
+    const bool fits = std::max(t.m, std::max(t.n, t.k)) <= kSmallMax;
+    if (p->small_ok && !cplx && !p->herk && fits &&
+        (r == 1 || (r == 0 && split_small_route(s, t.m, t.n, t.k)))) {
       small.push_back((int32_t)i);
       continue;
     }
@@ -833,7 +837,7 @@ static void grids(SplitPlan* p) {
 bg_status split_plan_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr,
                             const std::vector<bg_instance>& table, const int64_t* d_table,
                             int sms, bool autotune, cudaStream_t st, std::string* err,
-                            bool herk, bool small_kernel) {
+                            bool herk, bool small_kernel, const std::vector<int8_t>* route) {
   (void)d_table;
   (void)autotune;
   (void)st;
@@ -844,6 +848,7 @@ bg_status split_plan_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr
   }
   p->herk = herk;
   p->small_ok = small_kernel && split_small_supported(p->s, p->beta);
+  if (route) p->route = *route;
   bg_status s = build_instances(p, table, err);
   if (s != BG_OK) {
     split_plan_destroy(p);

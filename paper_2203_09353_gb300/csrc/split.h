@@ -26,10 +26,18 @@ struct SplitWorkspace {
 // Digit width used for `slices` planes when the caller passes beta_bits = 0.
 int split_default_beta(int slices);
 
+namespace splitk {
+// Slice counts and digit widths the small-instance kernel has versions for.
+bool split_small_supported(int s, int beta);
+}  // namespace splitk
+
 bg_status split_plan_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr,
                             const std::vector<bg_instance>& table, const int64_t* d_table,
                             int sms, bool autotune, cudaStream_t st, std::string* err, bool herk = false,
-                            bool small_kernel = true);
+                            bool small_kernel = true, const std::vector<int8_t>* route = nullptr);
+// route (optional, one entry per table instance): 0 = the small-instance
+// kernel where split_small_route says so, 1 = the small-instance kernel for
+// every instance it can take (real, m, n, k <= 64), 2 = the tile kernels.
 bg_status split_chain_create(SplitPlan** out, bg_dtype dt, const bg_precision& pr,
                              const std::vector<int64_t>& wn, const std::vector<int64_t>& woff,
                              const std::vector<int64_t>& pool_n,

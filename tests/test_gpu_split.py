@@ -175,10 +175,16 @@ def test_autotuned_plan_routes_and_matches_oracle(gpu, s, tmp_path):
     routes = {tuple(c["bucket"]): c["program"] for c in d["classes"]}
     for c in d["classes"]:
         names = [x["program"] for x in c["tried"]]
-        assert "split" in names and len(names) >= 2  # both paths were timed
+        assert any(nm.startswith("split") for nm in names) and len(names) >= 2  # both paths timed
+        if max(c["bucket"]) <= 64:  # small-instance kernel and tile kernels both timed
+            assert {"split_small", "split_tiles"} <= set(names), names
     e = errors(b, host(C), oracle_batch(b))
     assert e.max() <= TOL_SPLIT[s], (s, e.max())
-    n_split = sum(1 for v in routes.values() if v == "split")
+    n_split = sum(1 for v in routes.values() if v.startswith("split"))
+    if n_split:
+        # the classes given to the small-instance kernel are exactly its instances
+        want_small = sum(c["members"] for c in d["classes"] if c["program"] == "split_small")
+        assert d["split"]["small_instances"] == want_small
     sp = d.get("split")
     assert (sp is not None) == (n_split > 0)
     # split part: slicer, tile kernel, small-instance kernel (each when it has work); FP64 part

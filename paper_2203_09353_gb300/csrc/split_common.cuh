@@ -40,7 +40,7 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any singl
 // slices on one copy fills TMEM and the epilogue empties it level by level
 // (a double-buffered 6-slice tile would be 32 wide, which measured slower).
 __host__ __device__ constexpr int bn_for(int s) {
-  return s <= 2 ? 128 : s <= 4 ? 64 : s == 5 ? 48 : s == 6 ? 80 : s <= 8 ? 64 : s <= 10 ? 48 : 32;
+  return s <= 2 ? 128 : s <= 4 ? 64 : s == 5 ? 48 : s == 6 ? 48 : s <= 8 ? 64 : s <= 10 ? 48 : 32;
 }
 __host__ __device__ constexpr bool double_buffered(int s) { return s <= 5; }
 

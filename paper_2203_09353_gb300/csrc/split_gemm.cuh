@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(gemm_threads(H), 1) split_gemm_kernel(const Ge
 #define BG_DISPATCH_GEMM(s, ...)                                                    \
   switch (s) {                                                                      \
     case 3: { constexpr int BNV = bn_for(3), SFV = 3, HV = 4; constexpr bool DBV = true; __VA_ARGS__; } \
-    case 6: { constexpr int BNV = bn_for(6), SFV = 6, HV = 2; constexpr bool DBV = false; __VA_ARGS__; } \
+    case 6: { constexpr int BNV = bn_for(6), SFV = 6, HV = 3; constexpr bool DBV = false; __VA_ARGS__; } \
     case 9: { constexpr int BNV = bn_for(9), SFV = 9, HV = 3; constexpr bool DBV = false; __VA_ARGS__; } \
     case 1: case 2: { constexpr int BNV = 128, SFV = 0, HV = 2; constexpr bool DBV = true; __VA_ARGS__; } \
     case 4: { constexpr int BNV = 64, SFV = 0, HV = 2; constexpr bool DBV = true; __VA_ARGS__; }   \

@@ -427,9 +427,9 @@ bool split_small_supported(int s, int beta) {
 // 0.21-0.49x the time of the tile kernels on uniform batches of n = 16, 24,
 // 32 at 3, 6 and 9 slices). Edges 33..64 run padded to 64 here, one instance
 // per CTA; they come here only where that measured faster than the tiles
-// (whose column width is 48 at 9 slices, 80 at 6): above 48 at 9 slices
-// (n = 56, 64: 0.67-0.69x; n = 40, 48: 1.00x), above 40 at 6 slices
-// (n = 48..64: 0.56-0.68x; n = 40: 1.00x), always at 3 slices (n = 40..64:
+// (whose column width is 48 at 6 and 9 slices, 64 at 3): above 48 at 9
+// slices (n = 56, 64: 0.67-0.69x; n = 40, 48: 1.00x), above 40 at 6 slices
+// (n = 48..64: 0.57-0.87x; n = 40: 1.00x), always at 3 slices (n = 40..64:
 // 0.76-0.79x).
 bool split_small_route(int s, int64_t m, int64_t n, int64_t k) {
   const int64_t e = m > n ? (m > k ? m : k) : (n > k ? n : k);

@@ -119,7 +119,7 @@ __device__ __forceinline__ uint32_t norm_units(float al) {
 template <int GT>
 __device__ __forceinline__ void prefetch_next(const SmallArgs& g, int64_t next, int gid, int ng,
                                               int tg) {
-  if (next < 0) return;
+  if (next < 0 || g.skip_product) return;  // alpha == 0: A and B are not touched
   const SmallItem nx = g.items[next];
   for (int q = gid; q < nx.count; q += ng) {
     const SInst ni = g.inst[g.ids[nx.first + q]];

@@ -47,12 +47,12 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # Valid only while the split kernel sources hash to NCU_SOURCES_SHA; otherwise
 # the traffic is reported as null.
 NCU_EQ1_BYTES = 10314440704.0
-NCU_TRAFFIC_PER_BYTE = {"split9": {"gemm": (13590736384 + 2374531840) / NCU_EQ1_BYTES,
-                                   "slicer": (7140693504 + 10727183104) / NCU_EQ1_BYTES,
-                                   "small": (560802560 + 155676160) / NCU_EQ1_BYTES}}
+NCU_TRAFFIC_PER_BYTE = {"split9": {"gemm": (13589957376 + 2374727168) / NCU_EQ1_BYTES,
+                                   "slicer": (7149745920 + 10727013376) / NCU_EQ1_BYTES,
+                                   "small": (560837632 + 155502080) / NCU_EQ1_BYTES}}
 NCU_SOURCES = ("split.cu", "split_common.cuh", "split_gemm.cuh", "split_gemm_r64.cu",
                "split_small.cu")
-NCU_SOURCES_SHA = "31bb75d9fd1c5fe8"
+NCU_SOURCES_SHA = "39867e7f115557e5"
 
 
 def split_sources_sha() -> str:
@@ -1089,8 +1089,9 @@ def main():
         free_ev = [None, None]  # set k: its last GEMM and read-back of two steps ago
         stepc = [0]
 
-        # phased schedule: a step's copies in wait for the previous step's
-        # read-back, so that the two directions never share the host link
+        # phased schedule: a step's read-back waits for its last copy in, and
+        # the next step's copies in wait for that read-back, so that the two
+        # directions never share the host link
         phased = [False]
 
         def e2e_step():
@@ -1114,6 +1115,8 @@ def main():
                 evg = torch.cuda.Event()
                 evg.record(stream)
                 done_gemm.append(evg)
+            if phased[0]:
+                s_out.wait_event(done_in[-1])
             for (_, (_, _, (c0, c1))), evg in zip(chunks, done_gemm):
                 s_out.wait_event(evg)
                 with torch.cuda.stream(s_out):

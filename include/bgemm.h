@@ -273,12 +273,18 @@ bg_status apply_local_gate(bg_dtype dtype, int64_t walkers, int32_t spins, const
  *    at element w * stride (stride >= 2^spins); 2 <= spins <= 30,
  *    1 <= split <= min(spins - 1, 10). precision (NULL = FP64) selects the
  *    precision of G_w: it is formed by a Hermitian-update plan
- *    (BG_PLAN_HERK) in that mode. The eigenvalues are always computed in
- *    FP64: Householder reduction of G_w to a real tridiagonal matrix, then
- *    bisection on its Sturm sequence. flags: 0 or BG_PLAN_PROFILE (slot 0 of
+ *    (BG_PLAN_HERK) in that mode. The eigenvalues come from a Householder
+ *    reduction of G_w to a real tridiagonal matrix, then bisection on its
+ *    Sturm sequence, in FP64. In split mode with K > 64 the reduction is
+ *    blocked: panels of 16 columns in FP64, each followed by its rank-32
+ *    trailing update as a grouped complex GEMM in the plan's precision (a
+ *    panel kernel, a pack kernel and that GEMM's launches), and the last 64
+ *    columns unblocked. flags: 0 or BG_PLAN_PROFILE (slot 0 of
  *    bg_plan_kernel_times: G; slot 1: the eigenvalues and the entropy). The
  *    plan owns a workspace of walkers x K x K complex128 plus 2 walkers x K
- *    doubles (bg_plan_get_info). Must not be called during stream capture.
+ *    doubles, and for the blocked reduction the panels' vectors (walkers x
+ *    32 K complex128), the packed operand and the GEMM plans' workspace
+ *    (bg_plan_get_info). Must not be called during stream capture.
  *  - batched_entropy: states: DEVICE, 16-byte aligned; entropy: DEVICE
  *    double [walkers] (natural logarithm); eigenvalues: DEVICE double
  *    [walkers][K] or NULL: the K eigenvalues of each G_w, ascending, not

@@ -235,6 +235,15 @@ struct bg_plan {
   double* d_tri_d = nullptr;
   double* d_tri_e = nullptr;
   int ent_n = 0;
+  // the blocked reduction of split-precision entropy plans: one grouped GEMM
+  // plan per panel for the trailing update C[q:, q:] -= [V2 W2] [W2 V2]^H,
+  // every walker's [V W] (tri_pstride elements apart) and the packed
+  // second operand
+  std::vector<bg_plan*> tri_gemm;
+  int tri_nb = 0;
+  int64_t tri_pstride = 0;
+  double2* d_tri_p = nullptr;
+  double2* d_tri_wvh = nullptr;
   // annealing-step plans (Alg. 1): the entropy plan over the proposals, the
   // proposal buffer (walkers x 2^spins, contiguous) and the new energies
   bool is_anneal = false;
@@ -546,6 +555,9 @@ void destroy_plan(bg_plan* p) {
   cudaFree(p->d_pool_n);
   if (p->split) split_plan_destroy(p->split);
   if (p->gram) destroy_plan(p->gram);
+  for (bg_plan* g : p->tri_gemm) destroy_plan(g);
+  cudaFree(p->d_tri_p);
+  cudaFree(p->d_tri_wvh);
   if (p->ent) destroy_plan(p->ent);
   cudaFree(p->d_prop);
   cudaFree(p->d_enew);
@@ -1441,6 +1453,39 @@ bg_status entropy_plan(bg_plan** out, int64_t walkers, int32_t spins, int32_t sp
     }
     p->workspace_bytes = p->gram->workspace_bytes + (int64_t)(gb + 2 * tb);
     p->launches_per_call = p->gram->launches_per_call + 2;
+    if (pr.mode != BG_MODE_FP64 && K > kTriTail) {
+      // blocked reduction: panels of nb columns while more than kTriTail
+      // columns remain, each followed by its trailing update in the plan's
+      // precision; the last kTriTail columns are reduced unblocked
+      const int nb = kTriPanelWidth;
+      const int64_t pstride = 2 * (int64_t)nb * K;
+      const size_t pb = (size_t)walkers * pstride * sizeof(double2);
+      const size_t wb = (size_t)walkers * (K - nb) * 2 * nb * sizeof(double2);
+      if ((e = cudaMalloc(&p->d_tri_p, pb)) != cudaSuccess ||
+          (e = cudaMalloc(&p->d_tri_wvh, wb)) != cudaSuccess) {
+        destroy_plan(p);
+        return cuda_fail(e, "entropy plan workspace");
+      }
+      p->tri_nb = nb;
+      p->tri_pstride = pstride;
+      p->workspace_bytes += (int64_t)(pb + wb);
+      p->launches_per_call = p->gram->launches_per_call + 3;  // mirror, tail, bisection
+      for (int64_t p0 = 0; K - p0 > kTriTail; p0 += nb) {
+        const int64_t q = p0 + nb, mt = K - q;
+        for (int64_t w = 0; w < walkers; ++w)
+          table[(size_t)w] = bg_instance{mt, mt, 2 * nb, K, 2 * nb, K, w * pstride + q,
+                                         w * mt * 2 * nb, w * K * K + q + q * K};
+        bg_plan* g = nullptr;
+        s = batched_gemm_plan(&g, BG_C128, walkers, table.data(), &pr, 0, nullptr, stream);
+        if (s != BG_OK) {
+          destroy_plan(p);
+          return s;
+        }
+        p->tri_gemm.push_back(g);
+        p->workspace_bytes += g->workspace_bytes;
+        p->launches_per_call += 2 + g->launches_per_call;  // panel, pack, GEMM
+      }
+    }
   }
   *out = p;
   return BG_OK;
@@ -1474,9 +1519,32 @@ bg_status batched_entropy(const bg_plan* plan, const void* states, double* entro
     BG_CUDA(cudaEventRecord(ev[1], st), "profiling event record");
     BG_CUDA(cudaEventRecord(ev[2], st), "profiling event record");
   }
-  cudaError_t e = launch_entropy_eig(p->d_gram, p->count, p->ent_n, p->d_tri_d, p->d_tri_e,
-                                     entropy, eigenvalues, st);
-  if (e != cudaSuccess) return cuda_fail(e, "entropy eigenvalue launch");
+  if (p->tri_gemm.empty()) {
+    cudaError_t e = launch_entropy_eig(p->d_gram, p->count, p->ent_n, p->d_tri_d, p->d_tri_e,
+                                       entropy, eigenvalues, st);
+    if (e != cudaSuccess) return cuda_fail(e, "entropy eigenvalue launch");
+  } else {
+    const int n = p->ent_n, nb = p->tri_nb;
+    const double minus_one[2] = {-1.0, 0.0};
+    cudaError_t e0 = launch_tri_mirror(p->d_gram, p->count, n, st);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "entropy mirror launch");
+    int p0 = 0;
+    for (bg_plan* g : p->tri_gemm) {
+      cudaError_t e = launch_tri_panel(p->d_gram, p->count, n, p0, nb, p->d_tri_p,
+                                       p->tri_pstride, p->d_tri_d, p->d_tri_e, st);
+      if (e == cudaSuccess)
+        e = launch_tri_pack(p->d_tri_p, p->tri_pstride, p->count, n, p0 + nb, nb, p->d_tri_wvh,
+                            st);
+      if (e != cudaSuccess) return cuda_fail(e, "entropy panel launch");
+      s = batched_gemm_grouped(g, p->d_tri_p, p->d_tri_wvh, p->d_gram, minus_one, one, stream);
+      if (s != BG_OK) return s;
+      p0 += nb;
+    }
+    cudaError_t e = launch_tri_tail(p->d_gram, p->count, n, p0, p->d_tri_d, p->d_tri_e, st);
+    if (e == cudaSuccess)
+      e = launch_entropy_bisect(p->d_tri_d, p->d_tri_e, p->count, n, entropy, eigenvalues, st);
+    if (e != cudaSuccess) return cuda_fail(e, "entropy eigenvalue launch");
+  }
   if (ev) BG_CUDA(cudaEventRecord(ev[3], st), "profiling event record");
   return BG_OK;
 }

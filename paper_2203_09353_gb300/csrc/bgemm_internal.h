@@ -129,6 +129,33 @@ bg_status static_scratch(void** out, size_t* bytes, std::string* err);
 cudaError_t launch_entropy_eig(double2* gram, int64_t walkers, int n, double* d, double* e,
                                double* entropy, double* eigs, cudaStream_t st);
 
+// The blocked form of the same reduction (entropy.cu). Panels of nb columns:
+// launch_tri_panel reduces columns p0 .. p0 + nbp - 1 (p0 + nbp <= n - 1) of
+// every walker, keeping the panel's rank-2 updates as [V W] (walker w at
+// P + w pstride, 2 nbp columns of n, pstride >= 2 nbp n). launch_tri_pack
+// writes the trailing update's second operand [W2 V2]^H for the rows from
+// q = p0 + nbp (walker w at wvh + w (n - q) 2 nbp), after which the caller
+// applies C[q:, q:] -= [V2 W2] [W2 V2]^H as a batched GEMM. launch_tri_tail
+// reduces the trailing matrix from row and column p0 unblocked, and
+// launch_entropy_bisect takes the tridiagonal matrices to eigenvalues and
+// entropies.
+// Panel width of the blocked reduction (at most 64): at K = 256 (128
+// walkers), 16 columns beat 8 (more trailing GEMMs) and 32 (the corrections
+// grow with the width). The last kTriTail columns are reduced unblocked.
+constexpr int kTriPanelWidth = 16;
+constexpr int kTriTail = 64;
+cudaError_t launch_tri_panel(double2* gram, int64_t walkers, int n, int p0, int nbp, double2* P,
+                             int64_t pstride, double* d, double* e, cudaStream_t st);
+cudaError_t launch_tri_tail(double2* gram, int64_t walkers, int n, int p0, double* d, double* e,
+                            cudaStream_t st);
+// Copies each walker's lower triangle into its upper triangle (conjugated):
+// the blocked panels read the trailing matrix in full.
+cudaError_t launch_tri_mirror(double2* gram, int64_t walkers, int n, cudaStream_t st);
+cudaError_t launch_tri_pack(const double2* P, int64_t pstride, int64_t walkers, int n, int q,
+                            int nbp, double2* wvh, cudaStream_t st);
+cudaError_t launch_entropy_bisect(const double* d, const double* e, int64_t walkers, int n,
+                                  double* entropy, double* eigs, cudaStream_t st);
+
 // Metropolis decision per walker and copy of the accepted proposals over the
 // current states (anneal.cu). prop / cur may be null when amps == 0.
 cudaError_t launch_metropolis(int64_t walkers, double T, int direction, const double* u,

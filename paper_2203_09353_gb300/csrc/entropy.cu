@@ -21,6 +21,7 @@
 // global memory (L2), one SM per walker.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -29,8 +30,15 @@
 namespace bg {
 namespace {
 
-constexpr int kEntThreads = 256;      // bisection; reduction for n > 512
-constexpr int kEntMaxThreads = 512;   // reduction for n <= 512
+constexpr int kEntThreads = 256;  // bisection
+// Warps per walker of the two reductions, and the tile width of herm_matvec.
+// Measured at K = 256 (128 walkers): 8 warps beat 4, 12 and 16 in both
+// (the tiled product holds 32 column sums per lane, about 196 registers),
+// and 16-column tiles were no faster than 32.
+constexpr int kRedWarps = 8;
+constexpr int kTileCols = 32;
+constexpr int kPanelWarps = 8;
+constexpr int kPanelMax = 64;  // widest panel of the blocked reduction
 
 struct Z {
   double re, im;
@@ -49,6 +57,25 @@ __device__ double block_sum(double v, double* red) {
   double s = 0.0;
   for (int i = 0; i < nw; ++i) s += red[i];  // fixed order: same value in every thread
   return s;
+}
+
+// Sums of a and b over the block at once (one pair of barriers); red: one
+// double2 per warp.
+__device__ void block_sum2(double& a, double& b, double2* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = make_double2(a, b);
+  __syncthreads();
+  a = 0.0;
+  b = 0.0;
+  for (int i = 0; i < nw; ++i) {
+    a += red[i].x;
+    b += red[i].y;
+  }
 }
 
 __device__ double block_max(double v, double* red) {
@@ -79,36 +106,135 @@ __device__ __forceinline__ Z zfma_conj(Z a, Z b, Z acc) {
 }
 
 
-// Householder tridiagonalisation of the n x n Hermitian matrices G_w (lower
-// triangle, column-major, leading dimension n, walker w at G + w n n; only the
-// lower triangle is read or written). Writes d[w n + i] (diagonal) and
-// e[w n + i] (sub-diagonal, i < n - 1). Each warp takes whole columns of the
-// trailing matrix (its lanes run down the column, coalesced): the Hermitian
-// product p = G22 v from the lower triangle alone adds G22[i, c] v[c] into
-// the warp's own partial vector for rows i >= c and conj(G22[i, c]) v[i]
-// into the column's dot product for row c; the rank-2 update then rewrites
-// the lower triangle. Dynamic shared memory: v, w and the warps' partial
-// products, (2 + WARPS) n complex.
+// Partial products of y = A v for the m x m Hermitian matrix A (lower
+// triangle, leading dimension ld; the upper triangle is never read): warp w
+// adds its share into part[w m + i], which must be zero on entry, so that y
+// is the sum over the warps. The lower triangle is cut into stripes of TJ
+// columns, and each stripe into tiles of 32 rows x TJ columns whose rows
+// start at the stripe's diagonal. A lane takes one row i of a tile: it adds
+// A[i, j] v[j] over the tile's columns into its row's sum (stored once per
+// tile), and conj(A[i, j]) v[i] into one accumulator per column j. The tiles,
+// in stripe order, are dealt to the warps in equal contiguous runs; a warp
+// forms its column sums over the lanes when it leaves a stripe, by a
+// butterfly in which each step halves the values a lane keeps (TJ - 1
+// complex additions for TJ = 32), so that the FP64 pipe spends almost all
+// its issue slots on the products.
+template <int WARPS, int TJ>
+__device__ __forceinline__ void herm_matvec(const double2* A, int ld, int m, const Z* v, Z* part) {
+  static_assert(TJ == 16 || TJ == 32, "tile width");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = (m + TJ - 1) / TJ;
+  auto chunks = [&](int s) { return (m - TJ * s + 31) >> 5; };  // tiles of stripe s
+  int total = 0;
+  for (int s = 0; s < S; ++s) total += chunks(s);
+  const int t0 = (int)((int64_t)total * warp / WARPS);
+  const int t1 = (int)((int64_t)total * (warp + 1) / WARPS);
+  if (t0 >= t1) return;
+  int s = 0, first = 0;
+  while (first + chunks(s) <= t0) first += chunks(s++);
+  int k = t0 - first;
+  Z* pw = part + warp * m;
+  Z acc[TJ];
+#pragma unroll
+  for (int jj = 0; jj < TJ; ++jj) acc[jj] = {0.0, 0.0};
+  for (int tile = t0; tile < t1; ++tile) {
+    const int j0 = TJ * s, i0 = j0 + 32 * k;
+    const int i = i0 + lane;
+    const bool row_ok = i < m;
+    const Z vi = row_ok ? v[i] : Z{0.0, 0.0};
+    const double2* arow = A + i + (size_t)j0 * ld;
+    Z y0 = {0.0, 0.0}, y1 = {0.0, 0.0};
+    if (i0 > j0 && i0 + 32 <= m) {  // a whole tile below the diagonal
+#pragma unroll
+      for (int jj = 0; jj < TJ; ++jj) {
+        const double2 a2 = arow[(size_t)jj * ld];
+        const Z a = {a2.x, a2.y};
+        if (jj & 1) y1 = zfma(a, v[j0 + jj], y1);
+        else y0 = zfma(a, v[j0 + jj], y0);
+        acc[jj] = zfma_conj(a, vi, acc[jj]);
+      }
+    } else {  // the diagonal tile, or the ragged last one
+#pragma unroll
+      for (int jj = 0; jj < TJ; ++jj) {
+        const int j = j0 + jj;
+        Z a = {0.0, 0.0};
+        if (row_ok && j < m && i >= j) {
+          const double2 a2 = arow[(size_t)jj * ld];
+          a = {a2.x, a2.y};
+        }
+        const Z vj = j < m ? v[j] : Z{0.0, 0.0};
+        if (jj & 1) y1 = zfma(a, vj, y1);
+        else y0 = zfma(a, vj, y0);
+        const Z at = i > j ? a : Z{0.0, 0.0};
+        acc[jj] = zfma_conj(at, vi, acc[jj]);
+      }
+    }
+    if (row_ok) pw[i] = zadd(pw[i], zadd(y0, y1));
+    if (++k == chunks(s) || tile + 1 == t1) {
+      // lane l ends with the sum over the lanes of acc[l mod TJ]: at the
+      // step of offset o, a lane whose bit o is set keeps the upper half of
+      // its live accumulators and receives its partner's upper half
+      if (TJ == 16) {
+#pragma unroll
+        for (int kk = 0; kk < TJ; ++kk) {
+          acc[kk].re += __shfl_xor_sync(0xFFFFFFFFu, acc[kk].re, 16);
+          acc[kk].im += __shfl_xor_sync(0xFFFFFFFFu, acc[kk].im, 16);
+        }
+      }
+#pragma unroll
+      for (int o = TJ / 2; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int kk = 0; kk < o; ++kk) {
+          const Z send = up ? acc[kk] : acc[kk + o];
+          const Z keep = up ? acc[kk + o] : acc[kk];
+          Z recv;
+          recv.re = __shfl_xor_sync(0xFFFFFFFFu, send.re, o);
+          recv.im = __shfl_xor_sync(0xFFFFFFFFu, send.im, o);
+          acc[kk] = zadd(keep, recv);
+        }
+      }
+      __syncwarp();
+      if (lane < TJ && j0 + lane < m) pw[j0 + lane] = zadd(pw[j0 + lane], acc[0]);
+      __syncwarp();
+#pragma unroll
+      for (int jj = 0; jj < TJ; ++jj) acc[jj] = {0.0, 0.0};
+      ++s;
+      k = 0;
+    }
+  }
+}
+
+// Householder tridiagonalisation of n x n Hermitian matrices: for walker w,
+// rows and columns off .. off + n - 1 of its ld x ld matrix at G + w ld ld
+// (lower triangle, column-major; only the lower triangle is read or
+// written). Writes d[w ld + off + i] (diagonal) and e[w ld + off + i]
+// (sub-diagonal, i < n - 1; e of the last row is set to 0). The product
+// p = G22 v comes from herm_matvec; the rank-2 update then rewrites the lower
+// triangle, a warp per column with its lanes down the column (coalesced).
+// Dynamic shared memory: v, w and the warps' partial products, (2 + WARPS) n
+// complex.
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) tridiag_kernel(double2* G, int n, double* d,
-                                                             double* e) {
+__global__ void __launch_bounds__(WARPS * 32) tridiag_kernel(double2* G, int n, int ld, int off,
+                                                             double* d, double* e) {
   constexpr int kEntWarps = WARPS;
   extern __shared__ double2 sm[];
   Z* v = reinterpret_cast<Z*>(sm);
   Z* w = v + n;
   Z* part = w + n;  // kEntWarps x n
   __shared__ double red[kEntWarps];
+  __shared__ double2 red2[kEntWarps];
   __shared__ double s_beta, s_tau_re, s_tau_im, s_sc_re, s_sc_im;
   __shared__ int s_skip;
-  double2* A = G + (size_t)blockIdx.x * n * n;
-  double* dw = d + (size_t)blockIdx.x * n;
-  double* ew = e + (size_t)blockIdx.x * n;
+  double2* A = G + (size_t)blockIdx.x * ld * ld + off + (size_t)off * ld;
+  double* dw = d + (size_t)blockIdx.x * ld + off;
+  double* ew = e + (size_t)blockIdx.x * ld + off;
   const int t = threadIdx.x, T = blockDim.x, warp = t >> 5, lane = t & 31;
-  auto at = [&](int r, int c) -> double2& { return A[r + (size_t)c * n]; };
+  auto at = [&](int r, int c) -> double2& { return A[r + (size_t)c * ld]; };
 
   for (int j = 0; j < n - 1; ++j) {
     const int m = n - j - 1;  // order of the trailing matrix G22 = A[j+1:, j+1:]
-    double2* A22 = A + (j + 1) + (size_t)(j + 1) * n;
+    double2* A22 = A + (j + 1) + (size_t)(j + 1) * ld;
     // ---- reflector of the column below the diagonal (zlarfg)
     double xn2 = 0.0;
     for (int i = 1 + t; i < m; i += T) {
@@ -148,27 +274,8 @@ __global__ void __launch_bounds__(WARPS * 32) tridiag_kernel(double2* G, int n, 
     }
     for (int i = t; i < kEntWarps * m; i += T) part[i] = {0.0, 0.0};
     __syncthreads();
-    // ---- partial products of p = G22 v from the lower triangle, a warp per column
-    Z* pw = part + warp * m;
-    for (int c = warp; c < m; c += kEntWarps) {
-      const double2* col = A22 + (size_t)c * n;
-      const Z vc = v[c];
-      Z dot = {0.0, 0.0};
-      for (int i = c + lane; i < m; i += 32) {
-        const double2 a2 = col[i];
-        const Z a = {a2.x, a2.y};
-        pw[i] = zfma(a, vc, pw[i]);                // G22[i, c] v[c], row i
-        if (i > c) dot = zfma_conj(a, v[i], dot);  // conj(G22[i, c]) v[i], row c
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        dot.re += __shfl_xor_sync(0xFFFFFFFFu, dot.re, o);
-        dot.im += __shfl_xor_sync(0xFFFFFFFFu, dot.im, o);
-      }
-      __syncwarp();
-      if (lane == 0) pw[c] = zadd(pw[c], dot);
-      __syncwarp();
-    }
+    // ---- partial products of p = G22 v from the lower triangle
+    herm_matvec<kEntWarps, kTileCols>(A22, ld, m, v, part);
     __syncthreads();
     // ---- p = tau sum of the partials, alpha2 = -tau/2 (p^H v), w = p + alpha2 v
     double pr = 0.0, pi_ = 0.0;
@@ -182,14 +289,13 @@ __global__ void __launch_bounds__(WARPS * 32) tridiag_kernel(double2* G, int n, 
       pr += pv.re;
       pi_ += pv.im;
     }
-    pr = block_sum(pr, red);
-    pi_ = block_sum(pi_, red);
+    block_sum2(pr, pi_, red2);
     const Z alpha2 = zmul({-0.5 * tau.re, -0.5 * tau.im}, {pr, pi_});
     for (int i = t; i < m; i += T) w[i] = zfma(alpha2, v[i], w[i]);
     __syncthreads();
     // ---- G22 <- G22 - v w^H - w v^H on the lower triangle, a warp per column
     for (int c = warp; c < m; c += kEntWarps) {
-      double2* col = A22 + (size_t)c * n;
+      double2* col = A22 + (size_t)c * ld;
       const Z wc = {-w[c].re, w[c].im}, vc = {-v[c].re, v[c].im};  // -conj(w[c]), -conj(v[c])
       for (int i = c + lane; i < m; i += 32) {
         Z a = {col[i].x, col[i].y};
@@ -203,6 +309,271 @@ __global__ void __launch_bounds__(WARPS * 32) tridiag_kernel(double2* G, int n, 
   if (t == 0) {
     dw[n - 1] = at(n - 1, n - 1).x;
     ew[n - 1] = 0.0;
+  }
+}
+
+// Partial products of y = A v for an m x m matrix stored in full (leading
+// dimension ld): warp w takes the columns m w / W .. m (w + 1) / W - 1 and
+// writes its share of every row i < m to part[w m + i], so that y is the sum
+// over the warps. A lane takes the rows lane, lane + 32, ... (up to
+// kDenseRows of them at a time, independent sums), down each column; the
+// next column's elements are loaded while the current one is multiplied, so
+// that the L2 latency overlaps the FP64 work.
+constexpr int kDenseRows = 8;
+template <int WARPS>
+__device__ __forceinline__ void dense_matvec(const double2* A, int ld, int m, const Z* v, Z* part) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j0 = m * warp / WARPS, j1 = m * (warp + 1) / WARPS;
+  Z* pw = part + warp * m;
+  for (int r0 = 0; r0 < m; r0 += 32 * kDenseRows) {
+    Z y[kDenseRows];
+    double2 nx[kDenseRows];
+#pragma unroll
+    for (int c = 0; c < kDenseRows; ++c) {
+      y[c] = {0.0, 0.0};
+      nx[c] = make_double2(0.0, 0.0);
+    }
+    const double2* base = A + r0 + lane;
+    auto fetch = [&](int j) {
+      const double2* col = base + (size_t)j * ld;
+#pragma unroll
+      for (int c = 0; c < kDenseRows; ++c)
+        if (r0 + 32 * c + lane < m) nx[c] = col[32 * c];
+    };
+    if (j0 < j1) fetch(j0);
+    for (int j = j0; j < j1; ++j) {
+      double2 cur[kDenseRows];
+#pragma unroll
+      for (int c = 0; c < kDenseRows; ++c) cur[c] = nx[c];
+      if (j + 1 < j1) fetch(j + 1);
+      const Z vj = v[j];
+#pragma unroll
+      for (int c = 0; c < kDenseRows; ++c) y[c] = zfma({cur[c].x, cur[c].y}, vj, y[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kDenseRows; ++c)
+      if (r0 + 32 * c + lane < m) pw[r0 + 32 * c + lane] = y[c];
+  }
+}
+
+// ---- blocked reduction (panels of nb columns; the trailing rank-2nb update
+// runs as a batched GEMM on the tensor-core split path, see batched_entropy)
+//
+// One panel of the Householder reduction of each walker's G (lower triangle,
+// leading dimension n), columns c = p0 .. p0 + nbp - 1. The panel's rank-2
+// updates are not applied to the trailing matrix; they are kept as the
+// columns of V and W (walker w's V at P + w pstride, its W nbp columns
+// further, column t at + t n, rows below the column's diagonal), so that
+// [V W] is the first operand of the trailing update. For column c of the
+// panel:
+//  (a) column c (rows c..n-1) first receives this panel's earlier updates,
+//      A[r, c] -= sum_t V[r, t] conj(W[c, t]) + W[r, t] conj(V[c, t]);
+//  (b) the reflector of A[c+1:, c] gives d[c], e[c], tau and v, as in the
+//      unblocked kernel;
+//  (c) y = A22 v from the trailing matrix as it is in memory, corrected by
+//      the panel's earlier updates: y -= V2 (W2^H v) + W2 (V2^H v). The
+//      blocked path keeps both triangles of the trailing matrix (the Gram
+//      matrix is mirrored once, and the trailing updates write whole
+//      squares), so that this product runs over the full matrix;
+//  (d) w = tau y - (tau / 2) (w^H v) v is stored with v.
+// The panel ends before the matrix does (p0 + nbp <= n - 1), so every
+// column of it has rows below its diagonal.
+template <int WARPS, bool VWS>
+__global__ void __launch_bounds__(WARPS * 32) tri_panel_kernel(double2* G, int n, int p0, int nbp,
+                                                               double2* P, int64_t pstride,
+                                                               double* d, double* e) {
+  extern __shared__ double2 sm[];
+  Z* v = reinterpret_cast<Z*>(sm);
+  Z* y = v + n;
+  Z* part = y + n;  // WARPS x n
+  __shared__ Z cw[kPanelMax], cv[kPanelMax], s1[kPanelMax], s2[kPanelMax];
+  __shared__ double red[WARPS];
+  __shared__ double2 red2[WARPS];
+  __shared__ double s_beta, s_tau_re, s_tau_im, s_sc_re, s_sc_im;
+  __shared__ int s_skip;
+  double2* A = G + (size_t)blockIdx.x * n * n;
+  double2* V = P + (size_t)blockIdx.x * pstride;
+  double2* W = V + (size_t)nbp * n;
+  // the panel's V and W as the corrections read them: a copy of rows
+  // p0 .. n-1 in shared memory (VWS), else the global arrays themselves
+  const int ldl = VWS ? n - p0 : n, rb = VWS ? p0 : 0;
+  double2* Vl = VWS ? reinterpret_cast<double2*>(part + WARPS * n) : V;
+  double2* Wl = VWS ? Vl + (size_t)nbp * ldl : W;
+  auto vl = [&](int q, int r) -> double2& { return Vl[(size_t)q * ldl + r - rb]; };
+  auto wl = [&](int q, int r) -> double2& { return Wl[(size_t)q * ldl + r - rb]; };
+  double* dw = d + (size_t)blockIdx.x * n;
+  double* ew = e + (size_t)blockIdx.x * n;
+  const int t = threadIdx.x, T = blockDim.x, warp = t >> 5, lane = t & 31;
+  auto at = [&](int r, int c) -> double2& { return A[r + (size_t)c * n]; };
+  for (int i = 0; i < nbp; ++i) {
+    const int c = p0 + i;
+    const int m = n - c - 1;  // rows below the diagonal
+    // ---- (a) this panel's earlier rank-2 updates, applied to column c
+    if (i > 0) {
+      for (int q = t; q < i; q += T) {
+        const double2 wc = wl(q, c), vc = vl(q, c);
+        cw[q] = {wc.x, -wc.y};
+        cv[q] = {vc.x, -vc.y};
+      }
+      __syncthreads();
+      for (int r = c + t; r < n; r += T) {
+        Z a = {at(r, c).x, at(r, c).y}, b = {0.0, 0.0};  // two independent sums
+#pragma unroll 4
+        for (int q = 0; q < i; ++q) {
+          const double2 vr = vl(q, r), wr = wl(q, r);
+          a = zfma({-vr.x, -vr.y}, cw[q], a);
+          b = zfma({-wr.x, -wr.y}, cv[q], b);
+        }
+        at(r, c) = make_double2(a.re + b.re, a.im + b.im);
+      }
+      __syncthreads();
+    }
+    // ---- (b) reflector of the column below the diagonal
+    double xn2 = 0.0;
+    for (int r = c + 2 + t; r < n; r += T) {
+      const double2 x = at(r, c);
+      xn2 = fma(x.x, x.x, fma(x.y, x.y, xn2));
+    }
+    xn2 = block_sum(xn2, red);
+    if (t == 0) {
+      const double2 a = at(c + 1, c);
+      dw[c] = at(c, c).x;
+      if (xn2 == 0.0 && a.y == 0.0) {
+        s_skip = 1;
+        s_beta = a.x;
+      } else {
+        s_skip = 0;
+        const double beta = -copysign(sqrt(a.x * a.x + a.y * a.y + xn2), a.x);
+        s_beta = beta;
+        s_tau_re = (beta - a.x) / beta;
+        s_tau_im = -a.y / beta;
+        const double dr = a.x - beta, di = a.y, den = dr * dr + di * di;
+        s_sc_re = dr / den;
+        s_sc_im = -di / den;
+      }
+      ew[c] = s_beta;
+    }
+    __syncthreads();
+    if (s_skip) {  // H = I: v = w = 0 for this column
+      for (int r = c + 1 + t; r < n; r += T) {
+        V[(size_t)i * n + r] = make_double2(0.0, 0.0);
+        W[(size_t)i * n + r] = make_double2(0.0, 0.0);
+        if (VWS) vl(i, r) = wl(i, r) = make_double2(0.0, 0.0);
+      }
+      __syncthreads();
+      continue;
+    }
+    const Z tau = {s_tau_re, s_tau_im}, sc = {s_sc_re, s_sc_im};
+    for (int ii = t; ii < m; ii += T) {
+      Z vi = {1.0, 0.0};
+      if (ii > 0) {
+        const double2 x = at(c + 1 + ii, c);
+        vi = zmul({x.x, x.y}, sc);
+      }
+      v[ii] = vi;
+    }
+    __syncthreads();
+    // ---- (c) y = A22 v over the full trailing matrix, after the
+    // corrections' coefficients W2^H v and V2^H v (a warp per panel column)
+    for (int q = warp; q < i; q += WARPS) {
+      Z a1 = {0.0, 0.0}, a2 = {0.0, 0.0};
+      for (int ii = lane; ii < m; ii += 32) {
+        const double2 wr = wl(q, c + 1 + ii), vr = vl(q, c + 1 + ii);
+        a1 = zfma_conj({wr.x, wr.y}, v[ii], a1);
+        a2 = zfma_conj({vr.x, vr.y}, v[ii], a2);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a1.re += __shfl_xor_sync(0xFFFFFFFFu, a1.re, o);
+        a1.im += __shfl_xor_sync(0xFFFFFFFFu, a1.im, o);
+        a2.re += __shfl_xor_sync(0xFFFFFFFFu, a2.re, o);
+        a2.im += __shfl_xor_sync(0xFFFFFFFFu, a2.im, o);
+      }
+      if (lane == 0) {
+        s1[q] = a1;
+        s2[q] = a2;
+      }
+    }
+    dense_matvec<WARPS>(A + (c + 1) + (size_t)(c + 1) * n, n, m, v, part);
+    __syncthreads();
+    // ---- (d) w = tau (y - V2 s1 - W2 s2), alpha2 = -tau/2 (w^H v), w += alpha2 v
+    double pr = 0.0, pi_ = 0.0;
+    for (int ii = t; ii < m; ii += T) {
+      Z acc = {0.0, 0.0};
+#pragma unroll
+      for (int q = 0; q < WARPS; ++q) acc = zadd(acc, part[q * m + ii]);
+      const int r = c + 1 + ii;
+      Z acc2 = {0.0, 0.0};
+#pragma unroll 4
+      for (int q = 0; q < i; ++q) {
+        const double2 vr = vl(q, r), wr = wl(q, r);
+        acc = zfma({-vr.x, -vr.y}, s1[q], acc);
+        acc2 = zfma({-wr.x, -wr.y}, s2[q], acc2);
+      }
+      acc = zadd(acc, acc2);
+      const Z p = zmul(tau, acc);
+      y[ii] = p;
+      const Z pv = zfma_conj(p, v[ii], {0.0, 0.0});
+      pr += pv.re;
+      pi_ += pv.im;
+    }
+    block_sum2(pr, pi_, red2);
+    const Z alpha2 = zmul({-0.5 * tau.re, -0.5 * tau.im}, {pr, pi_});
+    for (int ii = t; ii < m; ii += T) {
+      const Z wv = zfma(alpha2, v[ii], y[ii]);
+      W[(size_t)i * n + c + 1 + ii] = make_double2(wv.re, wv.im);
+      V[(size_t)i * n + c + 1 + ii] = make_double2(v[ii].re, v[ii].im);
+      if (VWS) {
+        wl(i, c + 1 + ii) = make_double2(wv.re, wv.im);
+        vl(i, c + 1 + ii) = make_double2(v[ii].re, v[ii].im);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Copies the lower triangle of every walker's n x n matrix into its upper
+// triangle, A[j, i] = conj(A[i, j]) for i > j, a 32 x 32 tile per block
+// (blockIdx.x = tile of the lower triangle in row order, blockIdx.y =
+// walker) through shared memory, so that reads and writes are coalesced.
+__global__ void __launch_bounds__(256) tri_mirror_kernel(double2* G, int n) {
+  __shared__ double2 tile[32][33];
+  int idx = blockIdx.x, bi = 0;
+  while (idx > bi) idx -= ++bi;  // tile row bi holds bi + 1 tiles
+  const int bj = idx, i0 = 32 * bi, j0 = 32 * bj;
+  double2* A = G + (size_t)blockIdx.y * n * n;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int k = ty; k < 32; k += 8)
+    if (i0 + tx < n && j0 + k < n) tile[k][tx] = A[i0 + tx + (size_t)(j0 + k) * n];
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int r = j0 + tx, c = i0 + k;  // (r, c) above the diagonal takes conj(A[c, r])
+    if (r < n && c < n && c > r) {
+      const double2 x = tile[tx][k];
+      A[r + (size_t)c * n] = make_double2(x.x, -x.y);
+    }
+  }
+}
+
+// The second operand of the trailing update C -= [V2 W2] [W2 V2]^H, where V2
+// and W2 are rows q..n-1 of the panel's V and W (mt = n - q rows; the first
+// operand is [V W] itself, rows from q, leading dimension n): WVh is
+// 2 nbp x mt, column-major with leading dimension 2 nbp, walker w at
+// w mt 2 nbp; WVh[t, r] = conj(W[q + r, t]) for t < nbp and
+// conj(V[q + r, t - nbp]) above. A thread per (r, t) pair, t fastest, so
+// that the stores are coalesced.
+__global__ void tri_pack_kernel(const double2* P, int64_t pstride, int n, int q, int nbp,
+                                double2* WVh) {
+  const int mt = n - q, k2 = 2 * nbp;
+  const size_t w = blockIdx.y;
+  const double2* V = P + w * pstride;
+  const double2* W = V + (size_t)nbp * n;
+  double2* out = WVh + w * (size_t)mt * k2;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < mt * k2;
+       idx += gridDim.x * blockDim.x) {
+    const int tt = idx % k2, r = idx / k2;
+    const double2 x = tt < nbp ? W[(size_t)tt * n + q + r] : V[(size_t)(tt - nbp) * n + q + r];
+    out[idx] = make_double2(x.x, -x.y);
   }
 }
 
@@ -324,30 +695,100 @@ __global__ void __launch_bounds__(kEntThreads) bisect_kernel(const double* d, co
   if (t == 0) entropy[blockIdx.x] = s;
 }
 
+// The unblocked reduction of the n x n matrices at rows and columns
+// off .. off + n - 1 of every walker's ld x ld matrix.
+cudaError_t launch_tridiag(double2* gram, int64_t walkers, int n, int ld, int off, double* d,
+                           double* e, cudaStream_t st) {
+  const size_t sm = (2 + (size_t)kRedWarps) * n * sizeof(double2);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tridiag_kernel<kRedWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr = true;
+  }
+  tridiag_kernel<kRedWarps><<<(unsigned)walkers, kRedWarps * 32, sm, st>>>(gram, n, ld, off, d, e);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_entropy_eig(double2* gram, int64_t walkers, int n, double* d, double* e,
                                double* entropy, double* eigs, cudaStream_t st) {
   if (walkers <= 0) return cudaSuccess;
-  const int warps = n <= 512 ? kEntMaxThreads / 32 : kEntThreads / 32;
-  const size_t sm1 = (2 + (size_t)warps) * n * sizeof(double2);
-  const size_t sm2 = 3 * (size_t)n * sizeof(double) + (kEntThreads + 1) * sizeof(int);
+  cudaError_t err = launch_tridiag(gram, walkers, n, n, 0, d, e, st);
+  if (err != cudaSuccess) return err;
+  return launch_entropy_bisect(d, e, walkers, n, entropy, eigs, st);
+}
+
+namespace {
+constexpr size_t kPanelSmemMax = 220 * 1024;  // dynamic shared memory of the panel kernel
+template <int WARPS, bool VWS>
+void panel_launch(double2* gram, int64_t walkers, int n, int p0, int nbp, double2* P,
+                  int64_t pstride, double* d, double* e, size_t sm, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(tridiag_kernel<kEntMaxThreads / 32>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(tridiag_kernel<kEntThreads / 32>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tri_panel_kernel<WARPS, VWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kPanelSmemMax);
+    attr = true;
+  }
+  tri_panel_kernel<WARPS, VWS><<<(unsigned)walkers, WARPS * 32, sm, st>>>(gram, n, p0, nbp, P,
+                                                                           pstride, d, e);
+}
+}  // namespace
+
+cudaError_t launch_tri_panel(double2* gram, int64_t walkers, int n, int p0, int nbp, double2* P,
+                             int64_t pstride, double* d, double* e, cudaStream_t st) {
+  if (walkers <= 0) return cudaSuccess;
+  if (nbp < 1 || nbp > kPanelMax || p0 < 0 || p0 + nbp > n - 1 || pstride < 2 * (int64_t)nbp * n)
+    return cudaErrorInvalidValue;
+  // v, y and the warps' partial products; then, where they fit, the panel's
+  // V and W rows p0 .. n-1
+  const size_t base = (2 + (size_t)kPanelWarps) * n * sizeof(double2);
+  const size_t vw = 2 * (size_t)nbp * (n - p0) * sizeof(double2);
+  if (base > kPanelSmemMax) return cudaErrorInvalidValue;
+  if (base + vw <= kPanelSmemMax)
+    panel_launch<kPanelWarps, true>(gram, walkers, n, p0, nbp, P, pstride, d, e, base + vw, st);
+  else
+    panel_launch<kPanelWarps, false>(gram, walkers, n, p0, nbp, P, pstride, d, e, base, st);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri_pack(const double2* P, int64_t pstride, int64_t walkers, int n, int q,
+                            int nbp, double2* wvh, cudaStream_t st) {
+  if (walkers <= 0 || q >= n) return cudaSuccess;
+  const int64_t elems = (int64_t)(n - q) * 2 * nbp;
+  const unsigned bx = (unsigned)std::min<int64_t>((elems + 255) / 256, 64);
+  tri_pack_kernel<<<dim3(bx, (unsigned)walkers), 256, 0, st>>>(P, pstride, n, q, nbp, wvh);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri_mirror(double2* gram, int64_t walkers, int n, cudaStream_t st) {
+  if (walkers <= 0) return cudaSuccess;
+  const int T = (n + 31) / 32;
+  tri_mirror_kernel<<<dim3((unsigned)(T * (T + 1) / 2), (unsigned)walkers), 256, 0, st>>>(gram, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri_tail(double2* gram, int64_t walkers, int n, int p0, double* d, double* e,
+                            cudaStream_t st) {
+  if (walkers <= 0) return cudaSuccess;
+  if (p0 < 0 || p0 >= n) return cudaErrorInvalidValue;
+  return launch_tridiag(gram, walkers, n - p0, n, p0, d, e, st);
+}
+
+cudaError_t launch_entropy_bisect(const double* d, const double* e, int64_t walkers, int n,
+                                  double* entropy, double* eigs, cudaStream_t st) {
+  if (walkers <= 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
     cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     attr = true;
   }
-  if (warps == kEntMaxThreads / 32)
-    tridiag_kernel<kEntMaxThreads / 32><<<(unsigned)walkers, kEntMaxThreads, sm1, st>>>(gram, n, d, e);
-  else
-    tridiag_kernel<kEntThreads / 32><<<(unsigned)walkers, kEntThreads, sm1, st>>>(gram, n, d, e);
-  count_launch();
-  cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
+  const size_t sm2 = 3 * (size_t)n * sizeof(double) + (kEntThreads + 1) * sizeof(int);
   bisect_kernel<<<(unsigned)walkers, kEntThreads, sm2, st>>>(d, e, n, entropy, eigs);
   count_launch();
   return cudaGetLastError();

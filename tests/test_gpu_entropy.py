@@ -152,3 +152,32 @@ def test_argument_checks(gpu):
     with pytest.raises(bg.BgemmError) as ei:
         bg.batched_gemm_grouped(plan, st, None, st, 1.0, 0.0)
     assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("S,split", [(14, 7), (19, 9)])
+def test_blocked_reduction(gpu, S, split):
+    """Split-precision plans with K > 64 reduce G in panels, the trailing
+    updates running as batched GEMMs (K = 128: 4 panels; K = 512: 28 panels,
+    whose V and W leave shared memory for the wider ones). A diagonal G
+    (every reflector the identity), a rank-deficient Schmidt spectrum and a
+    random state, each against its closed form or the oracle, eigenvalue by
+    eigenvalue against a library eigensolver."""
+    rng = np.random.default_rng(110 + S)
+    M, K = 1 << (S - split), 1 << split
+    p_diag = rng.random(K) + 0.1
+    p_diag /= p_diag.sum()
+    P = np.zeros((M, K), dtype=np.complex128)
+    P[np.arange(K), np.arange(K)] = np.sqrt(p_diag)
+    p_low = rng.random(K // 3) ** 2
+    p_low /= p_low.sum()
+    states = [P.reshape(-1), schmidt_state(rng, p_low, S, split),
+              rng.standard_normal(1 << S) + 1j * rng.standard_normal(1 << S)]
+    want = [float(-np.sum(p_diag * np.log(p_diag))), float(-np.sum(p_low * np.log(p_low))),
+            oracle.entanglement_entropy(states[2], S, split)]
+    got, eig = run(states, S, split=split, prec=bg.precision("split", 9), eig=True)
+    assert np.max(np.abs(got - np.array(want))) <= TOL_ENT, (got, want)
+    for w, psi in enumerate(states):
+        X = psi.reshape(-1, K).T
+        lam = np.linalg.eigvalsh(X @ X.conj().T)
+        assert np.max(np.abs(eig[w] - lam)) <= 1e-12 * lam[-1], (w, np.max(np.abs(eig[w] - lam)))
+    assert np.allclose(eig[0], np.sort(p_diag), rtol=0, atol=1e-15)

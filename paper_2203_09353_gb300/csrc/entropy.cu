@@ -622,9 +622,34 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* e2, in
   return cnt;
 }
 
+// The same count in FP32 for the matrix scaled into [-1, 1] (d, e2 = e^2 as
+// floats), with a fast approximate division. Each step's rounding errors are
+// a few FP32 ulps relative to |d_i - x| <= 3 and to e^2, so the count is
+// exact for a matrix within about 7 x 2^-24 of the scaled one in the 2-norm
+// (its eigenvalues move at most that far). pivmin = FLT_MIN: the scaled e^2
+// are at most 1, so that no quotient overflows.
+__device__ __forceinline__ int sturm_count32(const float* d, const float* e2, int n, float x) {
+  float q = d[0] - x;
+  if (fabsf(q) < FLT_MIN) q = -FLT_MIN;
+  int cnt = q < 0.0f;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - x) - __fdividef(e2[i - 1], q);
+    if (fabsf(q) < FLT_MIN) q = -FLT_MIN;
+    cnt += q < 0.0f;
+  }
+  return cnt;
+}
+
 // Eigenvalues of each walker's tridiagonal matrix by bisection, then
-// S = -sum p ln p with p = lambda / sum(lambda) over p > 0. Dynamic shared
-// memory: d, e^2 and the eigenvalues, 3 n doubles, then T + 1 int counts.
+// S = -sum p ln p with p = lambda / sum(lambda) over p > 0. The brackets are
+// first narrowed in FP32 on the matrix scaled by a power of two into
+// [-1, 1]: from there a bracket [a, b] with count32(a) <= k < count32(b)
+// holds lambda_k within [a - del, b + del] (del = 32 x 2^-24, above the
+// FP32 count's error bound), and FP64 bisection takes it on to the
+// tolerance. That saves about 10 of the 45 FP64 Sturm counts per
+// eigenvalue. Matrices whose scale lies outside [2^-1000, 2^1000] skip the
+// FP32 stage. Dynamic shared memory: d, e^2 and the eigenvalues (3 n
+// doubles), T + 1 int counts, then d and e^2 as scaled floats (2 n).
 __global__ void __launch_bounds__(kEntThreads) bisect_kernel(const double* d, const double* e,
                                                              int n, double* entropy,
                                                              double* eigs) {
@@ -655,17 +680,37 @@ __global__ void __launch_bounds__(kEntThreads) bisect_kernel(const double* d, co
   const double tol = 2.0 * DBL_EPSILON * scale + 2.0 * pivmin;
   lo -= tol;
   hi += tol;
-  __syncthreads();
-  // multisection: one Sturm count per thread on an even grid of [lo, hi]
-  // gives every eigenvalue a bracket T times narrower to start from
   int* cnt = reinterpret_cast<int*>(lam + n);  // T + 1 counts
+  float* d32 = reinterpret_cast<float*>(cnt + T + 1);
+  float* e32 = d32 + n;
+  int ex = 0;
+  frexp(scale, &ex);
+  const bool use32 = scale > 0x1p-1000 && scale < 0x1p1000;
+  const double sc = ldexp(1.0, -ex);  // scale x sc in [0.5, 1)
+  if (use32) {
+    for (int i = t; i < n; i += T) {
+      d32[i] = (float)(sd[i] * sc);
+      const double es = (i + 1 < n ? ew[i] : 0.0) * sc;
+      e32[i] = (float)(es * es);
+    }
+  }
+  __syncthreads();
+  // multisection: one Sturm count per thread on an even grid gives every
+  // eigenvalue a bracket T times narrower to start from (the ends widened
+  // by twice the FP32 bound, so that the counts there are 0 and n)
+  const float del32 = 32.0f * 0x1p-24f;
+  const float lo32 = (float)(lo * sc) - 2.0f * del32, hi32 = (float)(hi * sc) + 2.0f * del32;
+  const float h32 = (hi32 - lo32) / (float)T;
   const double hstep = (hi - lo) / T;
-  cnt[t + 1] = t + 1 < T ? sturm_count(sd, se2, n, lo + (t + 1) * hstep, pivmin) : n;
+  auto grid32 = [&](int j) { return __fmaf_rn((float)j, h32, lo32); };
+  auto grid64 = [&](int j) { return fma((double)j, hstep, lo); };
+  if (use32) cnt[t + 1] = t + 1 < T ? sturm_count32(d32, e32, n, grid32(t + 1)) : n;
+  else cnt[t + 1] = t + 1 < T ? sturm_count(sd, se2, n, grid64(t + 1), pivmin) : n;
   if (t == 0) cnt[0] = 0;
   __syncthreads();
   for (int k = t; k < n; k += T) {
     // the k-th smallest eigenvalue: count(a) <= k < count(b)
-    int g = 0;  // last grid point with count <= k (counts are nondecreasing)
+    int g = 0;  // a grid cell with cnt[g] <= k < cnt[g + 1]
     int lo_i = 0, hi_i = T;
     while (hi_i - lo_i > 1) {
       const int mid = (lo_i + hi_i) >> 1;
@@ -673,7 +718,20 @@ __global__ void __launch_bounds__(kEntThreads) bisect_kernel(const double* d, co
       else hi_i = mid;
     }
     g = lo_i;
-    double a = lo + g * hstep, b = g + 1 < T ? lo + (g + 1) * hstep : hi;
+    double a, b;
+    if (use32) {
+      float a32 = grid32(g), b32 = g + 1 < T ? grid32(g + 1) : hi32;
+      for (int it = 0; it < 40 && b32 - a32 > del32; ++it) {
+        const float mid = 0.5f * (a32 + b32);
+        if (sturm_count32(d32, e32, n, mid) <= k) a32 = mid;
+        else b32 = mid;
+      }
+      a = ((double)a32 - (double)del32) / sc;  // dividing by a power of two: exact
+      b = ((double)b32 + (double)del32) / sc;
+    } else {
+      a = grid64(g);
+      b = g + 1 < T ? grid64(g + 1) : hi;
+    }
     for (int it = 0; it < 200 && b - a > tol; ++it) {
       const double mid = 0.5 * (a + b);
       if (sturm_count(sd, se2, n, mid, pivmin) <= k) a = mid;
@@ -788,7 +846,8 @@ cudaError_t launch_entropy_bisect(const double* d, const double* e, int64_t walk
     cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     attr = true;
   }
-  const size_t sm2 = 3 * (size_t)n * sizeof(double) + (kEntThreads + 1) * sizeof(int);
+  const size_t sm2 = 3 * (size_t)n * sizeof(double) + (kEntThreads + 1) * sizeof(int) +
+                     2 * (size_t)n * sizeof(float);
   bisect_kernel<<<(unsigned)walkers, kEntThreads, sm2, st>>>(d, e, n, entropy, eigs);
   count_launch();
   return cudaGetLastError();

@@ -252,12 +252,13 @@ __global__ void __launch_bounds__(WARPS * 32) tridiag_kernel(double2* G, int n, 
         s_skip = 0;
         const double beta = -copysign(sqrt(a.x * a.x + a.y * a.y + xn2), a.x);
         s_beta = beta;
-        s_tau_re = (beta - a.x) / beta;
-        s_tau_im = -a.y / beta;
+        const double rb = 1.0 / beta;
+        s_tau_re = (beta - a.x) * rb;
+        s_tau_im = -a.y * rb;
         // 1 / (alpha - beta)
-        const double dr = a.x - beta, di = a.y, den = dr * dr + di * di;
-        s_sc_re = dr / den;
-        s_sc_im = -di / den;
+        const double dr = a.x - beta, di = a.y, rden = 1.0 / (dr * dr + di * di);
+        s_sc_re = dr * rden;
+        s_sc_im = -di * rden;
       }
       ew[j] = s_beta;
     }
@@ -356,6 +357,121 @@ __device__ __forceinline__ void dense_matvec(const double2* A, int ld, int m, co
   }
 }
 
+// The unblocked reduction for n <= kSmallRed with the matrix held in shared
+// memory: the same steps as tridiag_kernel (rows and columns off .. off +
+// n - 1 of walker w's ld x ld matrix, lower triangle; d and e as there), a
+// CTA of 256 threads per walker. The Hermitian product gives each row four
+// threads (a quarter of the columns each, summed by two shuffles); the
+// rank-2 update gives each thread the rows r and m - 1 - r of one in eight
+// columns, so that every thread holds the same number of elements. The
+// global matrix is only read.
+constexpr int kSmallRed = 64;
+constexpr int kSmallLd = kSmallRed + 1;  // shared-memory leading dimension
+__global__ void __launch_bounds__(256) tridiag_small_kernel(const double2* G, int n, int ld,
+                                                            int off, double* d, double* e) {
+  extern __shared__ double2 sm_small[];  // kSmallRed x kSmallLd complex
+  Z* As = reinterpret_cast<Z*>(sm_small);
+  __shared__ Z v[kSmallRed], w[kSmallRed];
+  __shared__ double red[8];
+  __shared__ double2 red2[8];
+  __shared__ double s_beta, s_tau_re, s_tau_im, s_sc_re, s_sc_im;
+  __shared__ int s_skip;
+  const double2* A = G + (size_t)blockIdx.x * ld * ld + off + (size_t)off * ld;
+  double* dw = d + (size_t)blockIdx.x * ld + off;
+  double* ew = e + (size_t)blockIdx.x * ld + off;
+  const int t = threadIdx.x, T = blockDim.x;
+  for (int idx = t; idx < n * n; idx += T) {
+    const int r = idx % n, c = idx / n;
+    if (r >= c) {
+      const double2 x = A[r + (size_t)c * ld];
+      As[r + c * kSmallLd] = {x.x, x.y};
+    }
+  }
+  __syncthreads();
+  auto at = [&](int r, int c) -> Z& { return As[r + c * kSmallLd]; };
+  for (int j = 0; j < n - 1; ++j) {
+    const int m = n - j - 1;
+    const int b0 = j + 1;  // first row and column of G22
+    double xn2 = 0.0;
+    for (int i = 1 + t; i < m; i += T) {
+      const Z x = at(b0 + i, j);
+      xn2 = fma(x.re, x.re, fma(x.im, x.im, xn2));
+    }
+    xn2 = block_sum(xn2, red);
+    if (t == 0) {
+      const Z a = at(b0, j);
+      dw[j] = at(j, j).re;
+      if (xn2 == 0.0 && a.im == 0.0) {
+        s_skip = 1;
+        s_beta = a.re;
+      } else {
+        s_skip = 0;
+        const double beta = -copysign(sqrt(a.re * a.re + a.im * a.im + xn2), a.re);
+        s_beta = beta;
+        const double rb = 1.0 / beta;
+        s_tau_re = (beta - a.re) * rb;
+        s_tau_im = -a.im * rb;
+        const double dr = a.re - beta, di = a.im, rden = 1.0 / (dr * dr + di * di);
+        s_sc_re = dr * rden;
+        s_sc_im = -di * rden;
+      }
+      ew[j] = s_beta;
+    }
+    __syncthreads();
+    if (s_skip) continue;
+    const Z tau = {s_tau_re, s_tau_im}, sc = {s_sc_re, s_sc_im};
+    for (int i = t; i < m; i += T) v[i] = i == 0 ? Z{1.0, 0.0} : zmul(at(b0 + i, j), sc);
+    __syncthreads();
+    // p = G22 v: row r, a quarter q of the columns
+    const int r = t >> 2, q = t & 3;
+    Z y = {0.0, 0.0};
+    if (r < m) {
+      for (int cc = q; cc < m; cc += 4) {
+        if (cc <= r) y = zfma(at(b0 + r, b0 + cc), v[cc], y);
+        else y = zfma_conj(at(b0 + cc, b0 + r), v[cc], y);
+      }
+    }
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+      y.re += __shfl_xor_sync(0xFFFFFFFFu, y.re, o);
+      y.im += __shfl_xor_sync(0xFFFFFFFFu, y.im, o);
+    }
+    double pr = 0.0, pi_ = 0.0;
+    Z p = {0.0, 0.0};
+    if (r < m && q == 0) {
+      p = zmul(tau, y);
+      const Z pv = zfma_conj(p, v[r], {0.0, 0.0});
+      pr = pv.re;
+      pi_ = pv.im;
+    }
+    block_sum2(pr, pi_, red2);
+    const Z alpha2 = zmul({-0.5 * tau.re, -0.5 * tau.im}, {pr, pi_});
+    if (r < m && q == 0) w[r] = zfma(alpha2, v[r], p);
+    __syncthreads();
+    // G22 <- G22 - v w^H - w v^H on the lower triangle: thread (pair h,
+    // column group g) takes rows h and m - 1 - h, columns g, g + 8, ... up to
+    // the row
+    const int h = t & 31, g = t >> 5;
+    for (int s = 0; s < 2; ++s) {
+      const int rr = s == 0 ? h : m - 1 - h;
+      if (h > m - 1 - h || (s == 1 && rr == h)) continue;  // the pair's lower row takes both
+      const Z vr = v[rr], wr = w[rr];
+      for (int cc = g; cc <= rr; cc += 8) {
+        const Z wc = {-w[cc].re, w[cc].im}, vc = {-v[cc].re, v[cc].im};
+        Z a = at(b0 + rr, b0 + cc);
+        a = zfma(vr, wc, a);
+        a = zfma(wr, vc, a);
+        at(b0 + rr, b0 + cc) = a;
+      }
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    dw[n - 1] = at(n - 1, n - 1).re;
+    ew[n - 1] = 0.0;
+  }
+}
+
 // ---- blocked reduction (panels of nb columns; the trailing rank-2nb update
 // runs as a batched GEMM on the tensor-core split path, see batched_entropy)
 //
@@ -386,7 +502,7 @@ __global__ void __launch_bounds__(WARPS * 32) tri_panel_kernel(double2* G, int n
   Z* v = reinterpret_cast<Z*>(sm);
   Z* y = v + n;
   Z* part = y + n;  // WARPS x n
-  __shared__ Z cw[kPanelMax], cv[kPanelMax], s1[kPanelMax], s2[kPanelMax];
+  __shared__ Z s1[kPanelMax], s2[kPanelMax];
   __shared__ double red[WARPS];
   __shared__ double2 red2[WARPS];
   __shared__ double s_beta, s_tau_re, s_tau_im, s_sc_re, s_sc_im;
@@ -408,32 +524,30 @@ __global__ void __launch_bounds__(WARPS * 32) tri_panel_kernel(double2* G, int n
   for (int i = 0; i < nbp; ++i) {
     const int c = p0 + i;
     const int m = n - c - 1;  // rows below the diagonal
-    // ---- (a) this panel's earlier rank-2 updates, applied to column c
+    // ---- (a) this panel's earlier rank-2 updates, applied to column c,
+    // with the squared norm of its rows c+2.. for the reflector
+    double xn2 = 0.0;
     if (i > 0) {
-      for (int q = t; q < i; q += T) {
-        const double2 wc = wl(q, c), vc = vl(q, c);
-        cw[q] = {wc.x, -wc.y};
-        cv[q] = {vc.x, -vc.y};
-      }
-      __syncthreads();
       for (int r = c + t; r < n; r += T) {
         Z a = {at(r, c).x, at(r, c).y}, b = {0.0, 0.0};  // two independent sums
 #pragma unroll 4
         for (int q = 0; q < i; ++q) {
-          const double2 vr = vl(q, r), wr = wl(q, r);
-          a = zfma({-vr.x, -vr.y}, cw[q], a);
-          b = zfma({-wr.x, -wr.y}, cv[q], b);
+          const double2 vr = vl(q, r), wr = wl(q, r), wc = wl(q, c), vc = vl(q, c);
+          a = zfma({-vr.x, -vr.y}, {wc.x, -wc.y}, a);
+          b = zfma({-wr.x, -wr.y}, {vc.x, -vc.y}, b);
         }
-        at(r, c) = make_double2(a.re + b.re, a.im + b.im);
+        const double2 x = make_double2(a.re + b.re, a.im + b.im);
+        at(r, c) = x;
+        if (r >= c + 2) xn2 = fma(x.x, x.x, fma(x.y, x.y, xn2));
       }
-      __syncthreads();
+    } else {
+      for (int r = c + 2 + t; r < n; r += T) {
+        const double2 x = at(r, c);
+        xn2 = fma(x.x, x.x, fma(x.y, x.y, xn2));
+      }
     }
-    // ---- (b) reflector of the column below the diagonal
-    double xn2 = 0.0;
-    for (int r = c + 2 + t; r < n; r += T) {
-      const double2 x = at(r, c);
-      xn2 = fma(x.x, x.x, fma(x.y, x.y, xn2));
-    }
+    // ---- (b) reflector of the column below the diagonal (the block sum's
+    // barriers also publish column c)
     xn2 = block_sum(xn2, red);
     if (t == 0) {
       const double2 a = at(c + 1, c);
@@ -445,11 +559,12 @@ __global__ void __launch_bounds__(WARPS * 32) tri_panel_kernel(double2* G, int n
         s_skip = 0;
         const double beta = -copysign(sqrt(a.x * a.x + a.y * a.y + xn2), a.x);
         s_beta = beta;
-        s_tau_re = (beta - a.x) / beta;
-        s_tau_im = -a.y / beta;
-        const double dr = a.x - beta, di = a.y, den = dr * dr + di * di;
-        s_sc_re = dr / den;
-        s_sc_im = -di / den;
+        const double rb = 1.0 / beta;
+        s_tau_re = (beta - a.x) * rb;
+        s_tau_im = -a.y * rb;
+        const double dr = a.x - beta, di = a.y, rden = 1.0 / (dr * dr + di * di);
+        s_sc_re = dr * rden;
+        s_sc_im = -di * rden;
       }
       ew[c] = s_beta;
     }
@@ -757,6 +872,18 @@ __global__ void __launch_bounds__(kEntThreads) bisect_kernel(const double* d, co
 // off .. off + n - 1 of every walker's ld x ld matrix.
 cudaError_t launch_tridiag(double2* gram, int64_t walkers, int n, int ld, int off, double* d,
                            double* e, cudaStream_t st) {
+  if (n <= kSmallRed) {
+    const size_t sm = (size_t)kSmallRed * kSmallLd * sizeof(double2);
+    static bool attr_small = false;
+    if (!attr_small) {
+      cudaFuncSetAttribute(tridiag_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm);
+      attr_small = true;
+    }
+    tridiag_small_kernel<<<(unsigned)walkers, 256, sm, st>>>(gram, n, ld, off, d, e);
+    count_launch();
+    return cudaGetLastError();
+  }
   const size_t sm = (2 + (size_t)kRedWarps) * n * sizeof(double2);
   static bool attr = false;
   if (!attr) {

@@ -244,6 +244,7 @@ struct bg_plan {
   int64_t tri_pstride = 0;
   double2* d_tri_p = nullptr;
   double2* d_tri_wvh = nullptr;
+  double* d_tri_s = nullptr;  // Re G + Im G, walkers x K x K
   // annealing-step plans (Alg. 1): the entropy plan over the proposals, the
   // proposal buffer (walkers x 2^spins, contiguous) and the new energies
   bool is_anneal = false;
@@ -558,6 +559,7 @@ void destroy_plan(bg_plan* p) {
   for (bg_plan* g : p->tri_gemm) destroy_plan(g);
   cudaFree(p->d_tri_p);
   cudaFree(p->d_tri_wvh);
+  cudaFree(p->d_tri_s);
   if (p->ent) destroy_plan(p->ent);
   cudaFree(p->d_prop);
   cudaFree(p->d_enew);
@@ -1461,14 +1463,16 @@ bg_status entropy_plan(bg_plan** out, int64_t walkers, int32_t spins, int32_t sp
       const int64_t pstride = 2 * (int64_t)nb * K;
       const size_t pb = (size_t)walkers * pstride * sizeof(double2);
       const size_t wb = (size_t)walkers * (K - nb) * 2 * nb * sizeof(double2);
+      const size_t sb = (size_t)walkers * K * K * sizeof(double);
       if ((e = cudaMalloc(&p->d_tri_p, pb)) != cudaSuccess ||
-          (e = cudaMalloc(&p->d_tri_wvh, wb)) != cudaSuccess) {
+          (e = cudaMalloc(&p->d_tri_wvh, wb)) != cudaSuccess ||
+          (e = cudaMalloc(&p->d_tri_s, sb)) != cudaSuccess) {
         destroy_plan(p);
         return cuda_fail(e, "entropy plan workspace");
       }
       p->tri_nb = nb;
       p->tri_pstride = pstride;
-      p->workspace_bytes += (int64_t)(pb + wb);
+      p->workspace_bytes += (int64_t)(pb + wb + sb);
       p->launches_per_call = p->gram->launches_per_call + 3;  // mirror, tail, bisection
       for (int64_t p0 = 0; K - p0 > kTriTail; p0 += nb) {
         const int64_t q = p0 + nb, mt = K - q;
@@ -1483,7 +1487,7 @@ bg_status entropy_plan(bg_plan** out, int64_t walkers, int32_t spins, int32_t sp
         }
         p->tri_gemm.push_back(g);
         p->workspace_bytes += g->workspace_bytes;
-        p->launches_per_call += 2 + g->launches_per_call;  // panel, pack, GEMM
+        p->launches_per_call += 3 + g->launches_per_call;  // panel, pack, GEMM, sum
       }
     }
   }
@@ -1526,11 +1530,11 @@ bg_status batched_entropy(const bg_plan* plan, const void* states, double* entro
   } else {
     const int n = p->ent_n, nb = p->tri_nb;
     const double minus_one[2] = {-1.0, 0.0};
-    cudaError_t e0 = launch_tri_mirror(p->d_gram, p->count, n, st);
+    cudaError_t e0 = launch_tri_mirror(p->d_gram, p->d_tri_s, p->count, n, st);
     if (e0 != cudaSuccess) return cuda_fail(e0, "entropy mirror launch");
     int p0 = 0;
     for (bg_plan* g : p->tri_gemm) {
-      cudaError_t e = launch_tri_panel(p->d_gram, p->count, n, p0, nb, p->d_tri_p,
+      cudaError_t e = launch_tri_panel(p->d_gram, p->d_tri_s, p->count, n, p0, nb, p->d_tri_p,
                                        p->tri_pstride, p->d_tri_d, p->d_tri_e, st);
       if (e == cudaSuccess)
         e = launch_tri_pack(p->d_tri_p, p->tri_pstride, p->count, n, p0 + nb, nb, p->d_tri_wvh,
@@ -1538,6 +1542,8 @@ bg_status batched_entropy(const bg_plan* plan, const void* states, double* entro
       if (e != cudaSuccess) return cuda_fail(e, "entropy panel launch");
       s = batched_gemm_grouped(g, p->d_tri_p, p->d_tri_wvh, p->d_gram, minus_one, one, stream);
       if (s != BG_OK) return s;
+      e = launch_tri_sum(p->d_gram, p->d_tri_s, p->count, n, p0 + nb, st);
+      if (e != cudaSuccess) return cuda_fail(e, "entropy panel launch");
       p0 += nb;
     }
     cudaError_t e = launch_tri_tail(p->d_gram, p->count, n, p0, p->d_tri_d, p->d_tri_e, st);

@@ -144,13 +144,19 @@ cudaError_t launch_entropy_eig(double2* gram, int64_t walkers, int n, double* d,
 // grow with the width). The last kTriTail columns are reduced unblocked.
 constexpr int kTriPanelWidth = 16;
 constexpr int kTriTail = 64;
-cudaError_t launch_tri_panel(double2* gram, int64_t walkers, int n, int p0, int nbp, double2* P,
-                             int64_t pstride, double* d, double* e, cudaStream_t st);
+cudaError_t launch_tri_panel(double2* gram, const double* S, int64_t walkers, int n, int p0,
+                             int nbp, double2* P, int64_t pstride, double* d, double* e,
+                             cudaStream_t st);
 cudaError_t launch_tri_tail(double2* gram, int64_t walkers, int n, int p0, double* d, double* e,
                             cudaStream_t st);
 // Copies each walker's lower triangle into its upper triangle (conjugated):
-// the blocked panels read the trailing matrix in full.
-cudaError_t launch_tri_mirror(double2* gram, int64_t walkers, int n, cudaStream_t st);
+// the blocked panels read the trailing matrix in full, together with
+// S = Re G + Im G (walkers x n x n doubles, same layout), which the mirror
+// writes whole and launch_tri_sum rewrites on rows and columns q.. after
+// each trailing update.
+cudaError_t launch_tri_mirror(double2* gram, double* S, int64_t walkers, int n, cudaStream_t st);
+cudaError_t launch_tri_sum(const double2* gram, double* S, int64_t walkers, int n, int q,
+                           cudaStream_t st);
 cudaError_t launch_tri_pack(const double2* P, int64_t pstride, int64_t walkers, int n, int q,
                             int nbp, double2* wvh, cudaStream_t st);
 cudaError_t launch_entropy_bisect(const double* d, const double* e, int64_t walkers, int n,

@@ -313,47 +313,71 @@ __global__ void __launch_bounds__(WARPS * 32) tridiag_kernel(double2* G, int n, 
   }
 }
 
-// Partial products of y = A v for an m x m matrix stored in full (leading
-// dimension ld): warp w takes the columns m w / W .. m (w + 1) / W - 1 and
-// writes its share of every row i < m to part[w m + i], so that y is the sum
-// over the warps. A lane takes the rows lane, lane + 32, ... (up to
-// kDenseRows of them at a time, independent sums), down each column; the
-// next column's elements are loaded while the current one is multiplied, so
-// that the L2 latency overlaps the FP64 work.
+// Partial products of y = A v for an m x m complex matrix stored in full
+// (leading dimension ld), with S = Re A + Im A beside it (same layout) and
+// vs = Re v + Im v: three real products per element instead of four,
+//   Re y = sum Re A Re v - sum Im A Im v,
+//   Im y = sum S vs - sum Re A Re v - sum Im A Im v
+// (Gauss's form; its error is bounded normwise, c u |A| |v| with a small c,
+// which is what the reduction's backward stability needs). Warp w takes the
+// columns m w / W .. m (w + 1) / W - 1 and writes its share of every row
+// i < m to part[w m + i], so that y is the sum over the warps. A lane takes
+// the rows lane, lane + 32, ... (up to kDenseRows of them at a time,
+// independent sums), down each column; the next column's elements are
+// loaded while the current one is multiplied, so that the memory latency
+// overlaps the FP64 work.
 constexpr int kDenseRows = 8;
 template <int WARPS>
-__device__ __forceinline__ void dense_matvec(const double2* A, int ld, int m, const Z* v, Z* part) {
+__device__ __forceinline__ void dense_matvec(const double2* A, const double* S, int ld, int m,
+                                             const Z* v, const double* vs, Z* part) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j0 = m * warp / WARPS, j1 = m * (warp + 1) / WARPS;
   Z* pw = part + warp * m;
   for (int r0 = 0; r0 < m; r0 += 32 * kDenseRows) {
-    Z y[kDenseRows];
-    double2 nx[kDenseRows];
+    double t1[kDenseRows], t2[kDenseRows], t3[kDenseRows];
+    double2 na[kDenseRows];
+    double ns[kDenseRows];
 #pragma unroll
     for (int c = 0; c < kDenseRows; ++c) {
-      y[c] = {0.0, 0.0};
-      nx[c] = make_double2(0.0, 0.0);
+      t1[c] = t2[c] = t3[c] = 0.0;
+      na[c] = make_double2(0.0, 0.0);
+      ns[c] = 0.0;
     }
-    const double2* base = A + r0 + lane;
+    const double2* abase = A + r0 + lane;
+    const double* sbase = S + r0 + lane;
     auto fetch = [&](int j) {
-      const double2* col = base + (size_t)j * ld;
+      const double2* acol = abase + (size_t)j * ld;
+      const double* scol = sbase + (size_t)j * ld;
 #pragma unroll
       for (int c = 0; c < kDenseRows; ++c)
-        if (r0 + 32 * c + lane < m) nx[c] = col[32 * c];
+        if (r0 + 32 * c + lane < m) {
+          na[c] = acol[32 * c];
+          ns[c] = scol[32 * c];
+        }
     };
     if (j0 < j1) fetch(j0);
     for (int j = j0; j < j1; ++j) {
-      double2 cur[kDenseRows];
+      double2 ca[kDenseRows];
+      double cs[kDenseRows];
 #pragma unroll
-      for (int c = 0; c < kDenseRows; ++c) cur[c] = nx[c];
+      for (int c = 0; c < kDenseRows; ++c) {
+        ca[c] = na[c];
+        cs[c] = ns[c];
+      }
       if (j + 1 < j1) fetch(j + 1);
       const Z vj = v[j];
+      const double vsj = vs[j];
 #pragma unroll
-      for (int c = 0; c < kDenseRows; ++c) y[c] = zfma({cur[c].x, cur[c].y}, vj, y[c]);
+      for (int c = 0; c < kDenseRows; ++c) {
+        t1[c] = fma(ca[c].x, vj.re, t1[c]);
+        t2[c] = fma(ca[c].y, vj.im, t2[c]);
+        t3[c] = fma(cs[c], vsj, t3[c]);
+      }
     }
 #pragma unroll
     for (int c = 0; c < kDenseRows; ++c)
-      if (r0 + 32 * c + lane < m) pw[r0 + 32 * c + lane] = y[c];
+      if (r0 + 32 * c + lane < m)
+        pw[r0 + 32 * c + lane] = {t1[c] - t2[c], t3[c] - t1[c] - t2[c]};
   }
 }
 
@@ -495,12 +519,14 @@ __global__ void __launch_bounds__(256) tridiag_small_kernel(const double2* G, in
 // The panel ends before the matrix does (p0 + nbp <= n - 1), so every
 // column of it has rows below its diagonal.
 template <int WARPS, bool VWS>
-__global__ void __launch_bounds__(WARPS * 32) tri_panel_kernel(double2* G, int n, int p0, int nbp,
-                                                               double2* P, int64_t pstride,
-                                                               double* d, double* e) {
+__global__ void __launch_bounds__(WARPS * 32) tri_panel_kernel(double2* G, const double* Sg, int n,
+                                                               int p0, int nbp, double2* P,
+                                                               int64_t pstride, double* d,
+                                                               double* e) {
   extern __shared__ double2 sm[];
   Z* v = reinterpret_cast<Z*>(sm);
   Z* y = v + n;
+  double* vs = reinterpret_cast<double*>(y);  // Re v + Im v, while y is not in use
   Z* part = y + n;  // WARPS x n
   __shared__ Z s1[kPanelMax], s2[kPanelMax];
   __shared__ double red[WARPS];
@@ -586,6 +612,7 @@ __global__ void __launch_bounds__(WARPS * 32) tri_panel_kernel(double2* G, int n
         vi = zmul({x.x, x.y}, sc);
       }
       v[ii] = vi;
+      vs[ii] = vi.re + vi.im;
     }
     __syncthreads();
     // ---- (c) y = A22 v over the full trailing matrix, after the
@@ -609,7 +636,9 @@ __global__ void __launch_bounds__(WARPS * 32) tri_panel_kernel(double2* G, int n
         s2[q] = a2;
       }
     }
-    dense_matvec<WARPS>(A + (c + 1) + (size_t)(c + 1) * n, n, m, v, part);
+    dense_matvec<WARPS>(A + (c + 1) + (size_t)(c + 1) * n,
+                        Sg + (size_t)blockIdx.x * n * n + (c + 1) + (size_t)(c + 1) * n, n, m, v,
+                        vs, part);
     __syncthreads();
     // ---- (d) w = tau (y - V2 s1 - W2 s2), alpha2 = -tau/2 (w^H v), w += alpha2 v
     double pr = 0.0, pi_ = 0.0;
@@ -651,22 +680,44 @@ __global__ void __launch_bounds__(WARPS * 32) tri_panel_kernel(double2* G, int n
 // triangle, A[j, i] = conj(A[i, j]) for i > j, a 32 x 32 tile per block
 // (blockIdx.x = tile of the lower triangle in row order, blockIdx.y =
 // walker) through shared memory, so that reads and writes are coalesced.
-__global__ void __launch_bounds__(256) tri_mirror_kernel(double2* G, int n) {
+__global__ void __launch_bounds__(256) tri_mirror_kernel(double2* G, double* Sg, int n) {
   __shared__ double2 tile[32][33];
   int idx = blockIdx.x, bi = 0;
   while (idx > bi) idx -= ++bi;  // tile row bi holds bi + 1 tiles
   const int bj = idx, i0 = 32 * bi, j0 = 32 * bj;
   double2* A = G + (size_t)blockIdx.y * n * n;
+  double* S = Sg + (size_t)blockIdx.y * n * n;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int k = ty; k < 32; k += 8)
-    if (i0 + tx < n && j0 + k < n) tile[k][tx] = A[i0 + tx + (size_t)(j0 + k) * n];
+  for (int k = ty; k < 32; k += 8) {
+    const int r = i0 + tx, c = j0 + k;
+    if (r < n && c < n) {
+      const double2 x = A[r + (size_t)c * n];
+      tile[k][tx] = x;
+      if (r >= c) S[r + (size_t)c * n] = x.x + x.y;
+    }
+  }
   __syncthreads();
   for (int k = ty; k < 32; k += 8) {
     const int r = j0 + tx, c = i0 + k;  // (r, c) above the diagonal takes conj(A[c, r])
     if (r < n && c < n && c > r) {
       const double2 x = tile[tx][k];
       A[r + (size_t)c * n] = make_double2(x.x, -x.y);
+      S[r + (size_t)c * n] = x.x - x.y;
     }
+  }
+}
+
+// S = Re A + Im A on rows and columns q .. n-1 of every walker's matrix
+// (after a trailing update), a thread per element, coalesced down columns.
+__global__ void __launch_bounds__(256) tri_sum_kernel(const double2* G, double* Sg, int n, int q) {
+  const int mt = n - q;
+  const double2* A = G + (size_t)blockIdx.y * n * n + q + (size_t)q * n;
+  double* S = Sg + (size_t)blockIdx.y * n * n + q + (size_t)q * n;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < mt * mt;
+       idx += gridDim.x * blockDim.x) {
+    const int r = idx % mt, c = idx / mt;
+    const double2 x = A[r + (size_t)c * n];
+    S[r + (size_t)c * n] = x.x + x.y;
   }
 }
 
@@ -909,21 +960,22 @@ cudaError_t launch_entropy_eig(double2* gram, int64_t walkers, int n, double* d,
 namespace {
 constexpr size_t kPanelSmemMax = 220 * 1024;  // dynamic shared memory of the panel kernel
 template <int WARPS, bool VWS>
-void panel_launch(double2* gram, int64_t walkers, int n, int p0, int nbp, double2* P,
-                  int64_t pstride, double* d, double* e, size_t sm, cudaStream_t st) {
+void panel_launch(double2* gram, const double* S, int64_t walkers, int n, int p0, int nbp,
+                  double2* P, int64_t pstride, double* d, double* e, size_t sm, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(tri_panel_kernel<WARPS, VWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kPanelSmemMax);
     attr = true;
   }
-  tri_panel_kernel<WARPS, VWS><<<(unsigned)walkers, WARPS * 32, sm, st>>>(gram, n, p0, nbp, P,
+  tri_panel_kernel<WARPS, VWS><<<(unsigned)walkers, WARPS * 32, sm, st>>>(gram, S, n, p0, nbp, P,
                                                                            pstride, d, e);
 }
 }  // namespace
 
-cudaError_t launch_tri_panel(double2* gram, int64_t walkers, int n, int p0, int nbp, double2* P,
-                             int64_t pstride, double* d, double* e, cudaStream_t st) {
+cudaError_t launch_tri_panel(double2* gram, const double* S, int64_t walkers, int n, int p0,
+                             int nbp, double2* P, int64_t pstride, double* d, double* e,
+                             cudaStream_t st) {
   if (walkers <= 0) return cudaSuccess;
   if (nbp < 1 || nbp > kPanelMax || p0 < 0 || p0 + nbp > n - 1 || pstride < 2 * (int64_t)nbp * n)
     return cudaErrorInvalidValue;
@@ -933,9 +985,9 @@ cudaError_t launch_tri_panel(double2* gram, int64_t walkers, int n, int p0, int 
   const size_t vw = 2 * (size_t)nbp * (n - p0) * sizeof(double2);
   if (base > kPanelSmemMax) return cudaErrorInvalidValue;
   if (base + vw <= kPanelSmemMax)
-    panel_launch<kPanelWarps, true>(gram, walkers, n, p0, nbp, P, pstride, d, e, base + vw, st);
+    panel_launch<kPanelWarps, true>(gram, S, walkers, n, p0, nbp, P, pstride, d, e, base + vw, st);
   else
-    panel_launch<kPanelWarps, false>(gram, walkers, n, p0, nbp, P, pstride, d, e, base, st);
+    panel_launch<kPanelWarps, false>(gram, S, walkers, n, p0, nbp, P, pstride, d, e, base, st);
   count_launch();
   return cudaGetLastError();
 }
@@ -950,10 +1002,21 @@ cudaError_t launch_tri_pack(const double2* P, int64_t pstride, int64_t walkers, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_tri_mirror(double2* gram, int64_t walkers, int n, cudaStream_t st) {
+cudaError_t launch_tri_mirror(double2* gram, double* S, int64_t walkers, int n, cudaStream_t st) {
   if (walkers <= 0) return cudaSuccess;
   const int T = (n + 31) / 32;
-  tri_mirror_kernel<<<dim3((unsigned)(T * (T + 1) / 2), (unsigned)walkers), 256, 0, st>>>(gram, n);
+  tri_mirror_kernel<<<dim3((unsigned)(T * (T + 1) / 2), (unsigned)walkers), 256, 0, st>>>(gram, S,
+                                                                                         n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri_sum(const double2* gram, double* S, int64_t walkers, int n, int q,
+                           cudaStream_t st) {
+  if (walkers <= 0 || q >= n) return cudaSuccess;
+  const int64_t elems = (int64_t)(n - q) * (n - q);
+  const unsigned bx = (unsigned)std::min<int64_t>((elems + 255) / 256, 64);
+  tri_sum_kernel<<<dim3(bx, (unsigned)walkers), 256, 0, st>>>(gram, S, n, q);
   count_launch();
   return cudaGetLastError();
 }

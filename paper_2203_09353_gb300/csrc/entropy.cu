@@ -788,34 +788,103 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* e2, in
   return cnt;
 }
 
-// The same count in FP32 for the matrix scaled into [-1, 1] (d, e2 = e^2 as
-// floats), with a fast approximate division. Each step's rounding errors are
-// a few FP32 ulps relative to |d_i - x| <= 3 and to e^2, so the count is
-// exact for a matrix within about 7 x 2^-24 of the scaled one in the 2-norm
-// (its eigenvalues move at most that far). pivmin = FLT_MIN: the scaled e^2
-// are at most 1, so that no quotient overflows.
-__device__ __forceinline__ int sturm_count32(const float* d, const float* e2, int n, float x) {
-  float q = d[0] - x;
-  if (fabsf(q) < FLT_MIN) q = -FLT_MIN;
-  int cnt = q < 0.0f;
+// The same count by the three-term recurrence of the leading principal
+// minors, p_0 = 1, p_1 = d_0 - x, p_i = (d_{i-1} - x) p_{i-1} - e_{i-2}^2
+// p_{i-2}: the number of sign changes along p_0 .. p_n is the number of
+// negative pivots q_i = p_i / p_{i-1}, that is, of eigenvalues below x. No
+// division: a DADD, a DMUL and a DFMA a step, with the sign and zero tests
+// on the bit pattern. For the matrix scaled into [-1, 1] (|d - x| <= 3,
+// e^2 <= 1) a step changes |p| by a factor of at most 4 upwards, and a
+// cancellation leaves at least an ulp of its terms. A zero p_i is replaced
+// by -2^-60 p_{i-1} (the pivot -2^-60, below an ulp of the scaled entries:
+// the pivot form's rule for a zero pivot), an exact change of the sign and
+// exponent. Every 8 steps p and p_{i-1} are rescaled together by 2^-500 or
+// 2^500 when p's binary exponent has left [-500, 500]: in between, no p
+// leaves the normal range, and no sign changes. Each step is exact for
+// d - x and e^2 perturbed by a few ulps (the rounding factors of the p's
+// cancel in the ratios), so the count is exact for a matrix within a few
+// ulps of the scaled one.
+__device__ __forceinline__ void sturm3_step(double dx, double e2, double& p, double& pm,
+                                            long long& pb, int& neg, int& cnt) {
+  const double pn = fma(-e2, pm, dx * p);
+  long long nb = __double_as_longlong(pn);
+  if ((nb << 1) == 0) nb = (pb ^ (long long)0x8000000000000000ull) - (60ll << 52);  // -2^-60 p
+  const int s = (int)((unsigned long long)nb >> 63);
+  cnt += s ^ neg;
+  neg = s;
+  pm = p;
+  pb = nb;
+  p = __longlong_as_double(nb);
+}
+
+__device__ __forceinline__ int sturm_count3(const double* d, const double* e2, int n, double x) {
+  double pm = 1.0, p = d[0] - x;
+  long long pb = __double_as_longlong(p);
+  if ((pb << 1) == 0) pb = __double_as_longlong(-0x1p-60);
+  p = __longlong_as_double(pb);
+  int neg = (int)((unsigned long long)pb >> 63);
+  int cnt = neg;
+  int i = 1;
+  for (; i + 8 <= n; i += 8) {
+#pragma unroll 1
+    for (int u = 0; u < 8; ++u) sturm3_step(d[i + u] - x, e2[i + u - 1], p, pm, pb, neg, cnt);
+    const int ex = (int)((pb >> 52) & 0x7FF) - 1023;
+    if (ex > 500) {
+      p *= 0x1p-500;
+      pm *= 0x1p-500;
+      pb = __double_as_longlong(p);
+    } else if (ex < -500) {
+      p *= 0x1p500;
+      pm *= 0x1p500;
+      pb = __double_as_longlong(p);
+    }
+  }
+  for (; i < n; ++i) sturm3_step(d[i] - x, e2[i - 1], p, pm, pb, neg, cnt);
+  return cnt;
+}
+
+// The same recurrence in FP32 on the float copy of the scaled matrix, the
+// rescaling by 2^-60 / 2^60 checked at every step and a zero p_i replaced
+// by -2^-24 p_{i-1}. Its backward error, a few FP32 ulps of the scaled
+// entries, stays below the 32 x 2^-24 by which the FP32 brackets are
+// widened.
+__device__ __forceinline__ int sturm_count3f(const float* d, const float* e2, int n, float x) {
+  float pm = 1.0f, p = d[0] - x;
+  if (p == 0.0f) p = -0x1p-24f;
+  bool neg = p < 0.0f;
+  int cnt = neg;
   for (int i = 1; i < n; ++i) {
-    q = (d[i] - x) - __fdividef(e2[i - 1], q);
-    if (fabsf(q) < FLT_MIN) q = -FLT_MIN;
-    cnt += q < 0.0f;
+    float pn = fmaf(-e2[i - 1], pm, (d[i] - x) * p);
+    if (pn == 0.0f) pn = -0x1p-24f * p;
+    const bool s = pn < 0.0f;
+    cnt += s != neg;
+    neg = s;
+    pm = p;
+    p = pn;
+    const int ex = (int)((__float_as_uint(p) >> 23) & 0xFF) - 127;
+    if (ex > 60) {
+      p *= 0x1p-60f;
+      pm *= 0x1p-60f;
+    } else if (ex < -60) {
+      p *= 0x1p60f;
+      pm *= 0x1p60f;
+    }
   }
   return cnt;
 }
 
 // Eigenvalues of each walker's tridiagonal matrix by bisection, then
-// S = -sum p ln p with p = lambda / sum(lambda) over p > 0. The brackets are
-// first narrowed in FP32 on the matrix scaled by a power of two into
-// [-1, 1]: from there a bracket [a, b] with count32(a) <= k < count32(b)
-// holds lambda_k within [a - del, b + del] (del = 32 x 2^-24, above the
-// FP32 count's error bound), and FP64 bisection takes it on to the
-// tolerance. That saves about 10 of the 45 FP64 Sturm counts per
-// eigenvalue. Matrices whose scale lies outside [2^-1000, 2^1000] skip the
-// FP32 stage. Dynamic shared memory: d, e^2 and the eigenvalues (3 n
-// doubles), T + 1 int counts, then d and e^2 as scaled floats (2 n).
+// S = -sum p ln p with p = lambda / sum(lambda) over p > 0. The matrix is
+// scaled by a power of two into [-1, 1] and counted by the three-term
+// recurrence; the brackets are first narrowed in FP32: from there a bracket
+// [a, b] with count32(a) <= k < count32(b) holds lambda_k within
+// [a - del, b + del] (del = 32 x 2^-24, above the FP32 count's error
+// bound), and FP64 bisection takes it on to the tolerance. That saves about
+// 10 of the 45 FP64 Sturm counts per eigenvalue, and the recurrence halves
+// the FP64 instructions of a count. Matrices whose scale lies outside
+// [2^-1000, 2^1000] take the pivot form unscaled, in FP64 only. Dynamic
+// shared memory: d, e^2 and the eigenvalues (3 n doubles), T + 1 int
+// counts, then d and e^2 as scaled floats (2 n).
 __global__ void __launch_bounds__(kEntThreads) bisect_kernel(const double* d, const double* e,
                                                              int n, double* entropy,
                                                              double* eigs) {
@@ -853,11 +922,13 @@ __global__ void __launch_bounds__(kEntThreads) bisect_kernel(const double* d, co
   frexp(scale, &ex);
   const bool use32 = scale > 0x1p-1000 && scale < 0x1p1000;
   const double sc = ldexp(1.0, -ex);  // scale x sc in [0.5, 1)
-  if (use32) {
+  if (use32) {  // the scaled matrix, in place of d and e^2, and as floats
     for (int i = t; i < n; i += T) {
-      d32[i] = (float)(sd[i] * sc);
+      sd[i] *= sc;
       const double es = (i + 1 < n ? ew[i] : 0.0) * sc;
-      e32[i] = (float)(es * es);
+      se2[i] = es * es;
+      d32[i] = (float)sd[i];
+      e32[i] = (float)se2[i];
     }
   }
   __syncthreads();
@@ -870,7 +941,7 @@ __global__ void __launch_bounds__(kEntThreads) bisect_kernel(const double* d, co
   const double hstep = (hi - lo) / T;
   auto grid32 = [&](int j) { return __fmaf_rn((float)j, h32, lo32); };
   auto grid64 = [&](int j) { return fma((double)j, hstep, lo); };
-  if (use32) cnt[t + 1] = t + 1 < T ? sturm_count32(d32, e32, n, grid32(t + 1)) : n;
+  if (use32) cnt[t + 1] = t + 1 < T ? sturm_count3f(d32, e32, n, grid32(t + 1)) : n;
   else cnt[t + 1] = t + 1 < T ? sturm_count(sd, se2, n, grid64(t + 1), pivmin) : n;
   if (t == 0) cnt[0] = 0;
   __syncthreads();
@@ -889,21 +960,29 @@ __global__ void __launch_bounds__(kEntThreads) bisect_kernel(const double* d, co
       float a32 = grid32(g), b32 = g + 1 < T ? grid32(g + 1) : hi32;
       for (int it = 0; it < 40 && b32 - a32 > del32; ++it) {
         const float mid = 0.5f * (a32 + b32);
-        if (sturm_count32(d32, e32, n, mid) <= k) a32 = mid;
+        if (sturm_count3f(d32, e32, n, mid) <= k) a32 = mid;
         else b32 = mid;
       }
-      a = ((double)a32 - (double)del32) / sc;  // dividing by a power of two: exact
-      b = ((double)b32 + (double)del32) / sc;
+      // in scaled units from here
+      a = (double)a32 - (double)del32;
+      b = (double)b32 + (double)del32;
+      const double tol_s = tol * sc;
+      for (int it = 0; it < 200 && b - a > tol_s; ++it) {
+        const double mid = 0.5 * (a + b);
+        if (sturm_count3(sd, se2, n, mid) <= k) a = mid;
+        else b = mid;
+      }
+      lam[k] = 0.5 * (a + b) / sc;  // dividing by a power of two: exact
     } else {
       a = grid64(g);
       b = g + 1 < T ? grid64(g + 1) : hi;
+      for (int it = 0; it < 200 && b - a > tol; ++it) {
+        const double mid = 0.5 * (a + b);
+        if (sturm_count(sd, se2, n, mid, pivmin) <= k) a = mid;
+        else b = mid;
+      }
+      lam[k] = 0.5 * (a + b);
     }
-    for (int it = 0; it < 200 && b - a > tol; ++it) {
-      const double mid = 0.5 * (a + b);
-      if (sturm_count(sd, se2, n, mid, pivmin) <= k) a = mid;
-      else b = mid;
-    }
-    lam[k] = 0.5 * (a + b);
   }
   __syncthreads();
   double tot = 0.0;

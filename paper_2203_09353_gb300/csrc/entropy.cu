@@ -5,20 +5,24 @@
 // sum(lambda) and S = -sum p_i ln p_i.
 //
 // G comes from the library's Hermitian rank-k update (a grouped plan with
-// BG_PLAN_HERK, FP64 or split precision), lower triangle. Two kernels follow,
-// one CTA per walker:
-//  * tridiag_kernel: Householder reduction of G to a real symmetric
-//    tridiagonal matrix (d, e) in FP64, the steps of LAPACK's zhetd2 for the
-//    lower triangle: for column j, the reflector H = I - tau v v^H that maps
-//    G[j+1:, j] to (beta, 0, ..., 0) (beta real), then
-//    G22 <- G22 - v w^H - w v^H with p = tau G22 v, w = p - (tau/2)(p^H v) v.
-//    Only the lower triangle is touched: a warp per column of the trailing
-//    matrix, its lanes down the column (coalesced).
+// BG_PLAN_HERK, FP64 or split precision), lower triangle. Then, one CTA per
+// walker (one SM each):
+//  * the Householder reduction of G to a real symmetric tridiagonal matrix
+//    (d, e) in FP64, the steps of LAPACK's zhetd2 for the lower triangle:
+//    for column j, the reflector H = I - tau v v^H that maps G[j+1:, j] to
+//    (beta, 0, ..., 0) (beta real), then G22 <- G22 - v w^H - w v^H with
+//    p = tau G22 v, w = p - (tau/2)(p^H v) v. tridiag_kernel runs it column
+//    by column on the lower triangle; tridiag_small_kernel does the same
+//    for K <= 64 (and the blocked path's last 64 columns) in shared memory.
+//    Split-precision plans with K > 64 take the blocked form (zlatrd's
+//    steps): tri_panel_kernel reduces 16 columns at a time, keeping their
+//    rank-2 updates as [V W], and the trailing update C -= [V W][W V]^H
+//    runs as a grouped GEMM in the plan's precision between panels.
 //  * bisect_kernel: every eigenvalue of the tridiagonal matrix by bisection
-//    on the Sturm count (the number of negative pivots of T - x I), one thread
-//    per eigenvalue, then the entropy by a block reduction.
-// Both are FP64-pipe bound; the tridiagonal step holds a walker's G in
-// global memory (L2), one SM per walker.
+//    on the Sturm count (the number of eigenvalues below x), one thread per
+//    eigenvalue, then the entropy by a block reduction.
+// All of these are bound by the FP64 pipe (about 2 DFMA per clock per SM on
+// this part), not by memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -283,8 +283,9 @@ bg_status apply_local_gate(bg_dtype dtype, int64_t walkers, int32_t spins, const
  *    bg_plan_kernel_times: G; slot 1: the eigenvalues and the entropy). The
  *    plan owns a workspace of walkers x K x K complex128 plus 2 walkers x K
  *    doubles, and for the blocked reduction the panels' vectors (walkers x
- *    32 K complex128), the packed operand and the GEMM plans' workspace
- *    (bg_plan_get_info). Must not be called during stream capture.
+ *    32 K complex128), the packed operand, walkers x K x K doubles of
+ *    Re G + Im G and the GEMM plans' workspace (bg_plan_get_info). Must not
+ *    be called during stream capture.
  *  - batched_entropy: states: DEVICE, 16-byte aligned; entropy: DEVICE
  *    double [walkers] (natural logarithm); eigenvalues: DEVICE double
  *    [walkers][K] or NULL: the K eigenvalues of each G_w, ascending, not

@@ -35,12 +35,10 @@ namespace bg {
 namespace {
 
 constexpr int kEntThreads = 256;  // bisection
-// Warps per walker of the two reductions, and the tile width of herm_matvec.
-// Measured at K = 256 (128 walkers): 8 warps beat 4, 12 and 16 in both
-// (the tiled product holds 32 column sums per lane, about 196 registers),
-// and 16-column tiles were no faster than 32.
+// Warps per walker of the two reductions. Measured at K = 256 (128
+// walkers): 8 warps beat 4, 12 and 16 in both (the tiled product holds 32
+// column sums per lane, about 196 registers).
 constexpr int kRedWarps = 8;
-constexpr int kTileCols = 32;
 constexpr int kPanelWarps = 8;
 constexpr int kPanelMax = 64;  // widest panel of the blocked reduction
 
@@ -113,19 +111,19 @@ __device__ __forceinline__ Z zfma_conj(Z a, Z b, Z acc) {
 // Partial products of y = A v for the m x m Hermitian matrix A (lower
 // triangle, leading dimension ld; the upper triangle is never read): warp w
 // adds its share into part[w m + i], which must be zero on entry, so that y
-// is the sum over the warps. The lower triangle is cut into stripes of TJ
-// columns, and each stripe into tiles of 32 rows x TJ columns whose rows
-// start at the stripe's diagonal. A lane takes one row i of a tile: it adds
+// is the sum over the warps. The lower triangle is cut into stripes of
+// TJ = 32 columns, and each stripe into 32 x 32 tiles whose rows start at
+// the stripe's diagonal. A lane takes one row i of a tile: it adds
 // A[i, j] v[j] over the tile's columns into its row's sum (stored once per
 // tile), and conj(A[i, j]) v[i] into one accumulator per column j. The tiles,
 // in stripe order, are dealt to the warps in equal contiguous runs; a warp
 // forms its column sums over the lanes when it leaves a stripe, by a
-// butterfly in which each step halves the values a lane keeps (TJ - 1
-// complex additions for TJ = 32), so that the FP64 pipe spends almost all
+// butterfly in which each step halves the values a lane keeps (31 complex
+// additions for the 32 columns), so that the FP64 pipe spends almost all
 // its issue slots on the products.
-template <int WARPS, int TJ>
+template <int WARPS>
 __device__ __forceinline__ void herm_matvec(const double2* A, int ld, int m, const Z* v, Z* part) {
-  static_assert(TJ == 16 || TJ == 32, "tile width");
+  constexpr int TJ = 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int S = (m + TJ - 1) / TJ;
   auto chunks = [&](int s) { return (m - TJ * s + 31) >> 5; };  // tiles of stripe s
@@ -175,16 +173,9 @@ __device__ __forceinline__ void herm_matvec(const double2* A, int ld, int m, con
     }
     if (row_ok) pw[i] = zadd(pw[i], zadd(y0, y1));
     if (++k == chunks(s) || tile + 1 == t1) {
-      // lane l ends with the sum over the lanes of acc[l mod TJ]: at the
-      // step of offset o, a lane whose bit o is set keeps the upper half of
-      // its live accumulators and receives its partner's upper half
-      if (TJ == 16) {
-#pragma unroll
-        for (int kk = 0; kk < TJ; ++kk) {
-          acc[kk].re += __shfl_xor_sync(0xFFFFFFFFu, acc[kk].re, 16);
-          acc[kk].im += __shfl_xor_sync(0xFFFFFFFFu, acc[kk].im, 16);
-        }
-      }
+      // lane l ends with the sum over the lanes of acc[l]: at the step of
+      // offset o, a lane whose bit o is set keeps the upper half of its live
+      // accumulators and receives its partner's upper half
 #pragma unroll
       for (int o = TJ / 2; o >= 1; o >>= 1) {
         const bool up = (lane & o) != 0;
@@ -199,7 +190,7 @@ __device__ __forceinline__ void herm_matvec(const double2* A, int ld, int m, con
         }
       }
       __syncwarp();
-      if (lane < TJ && j0 + lane < m) pw[j0 + lane] = zadd(pw[j0 + lane], acc[0]);
+      if (j0 + lane < m) pw[j0 + lane] = zadd(pw[j0 + lane], acc[0]);
       __syncwarp();
 #pragma unroll
       for (int jj = 0; jj < TJ; ++jj) acc[jj] = {0.0, 0.0};
@@ -280,7 +271,7 @@ __global__ void __launch_bounds__(WARPS * 32) tridiag_kernel(double2* G, int n, 
     for (int i = t; i < kEntWarps * m; i += T) part[i] = {0.0, 0.0};
     __syncthreads();
     // ---- partial products of p = G22 v from the lower triangle
-    herm_matvec<kEntWarps, kTileCols>(A22, ld, m, v, part);
+    herm_matvec<kEntWarps>(A22, ld, m, v, part);
     __syncthreads();
     // ---- p = tau sum of the partials, alpha2 = -tau/2 (p^H v), w = p + alpha2 v
     double pr = 0.0, pi_ = 0.0;

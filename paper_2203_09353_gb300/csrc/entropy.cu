@@ -42,6 +42,21 @@ constexpr int kRedWarps = 8;
 constexpr int kPanelWarps = 8;
 constexpr int kPanelMax = 64;  // widest panel of the blocked reduction
 
+// A kernel's dynamic shared-memory limit is a property of the device: set it
+// once per device (at every call for ordinals beyond the table).
+constexpr int kAttrDevices = 64;
+template <typename Kernel>
+cudaError_t smem_limit(Kernel kernel, int bytes, bool (&done)[kAttrDevices]) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool tracked = dev >= 0 && dev < kAttrDevices;
+  if (tracked && done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && tracked) done[dev] = true;
+  return e;
+}
+
 struct Z {
   double re, im;
 };
@@ -999,23 +1014,17 @@ cudaError_t launch_tridiag(double2* gram, int64_t walkers, int n, int ld, int of
                            double* e, cudaStream_t st) {
   if (n <= kSmallRed) {
     const size_t sm = (size_t)kSmallRed * kSmallLd * sizeof(double2);
-    static bool attr_small = false;
-    if (!attr_small) {
-      cudaFuncSetAttribute(tridiag_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm);
-      attr_small = true;
-    }
+    static bool attr_small[kAttrDevices] = {};
+    const cudaError_t err = smem_limit(tridiag_small_kernel, (int)sm, attr_small);
+    if (err != cudaSuccess) return err;
     tridiag_small_kernel<<<(unsigned)walkers, 256, sm, st>>>(gram, n, ld, off, d, e);
     count_launch();
     return cudaGetLastError();
   }
   const size_t sm = (2 + (size_t)kRedWarps) * n * sizeof(double2);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tridiag_kernel<kRedWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    attr = true;
-  }
+  static bool attr[kAttrDevices] = {};
+  const cudaError_t err = smem_limit(tridiag_kernel<kRedWarps>, 200 * 1024, attr);
+  if (err != cudaSuccess) return err;
   tridiag_kernel<kRedWarps><<<(unsigned)walkers, kRedWarps * 32, sm, st>>>(gram, n, ld, off, d, e);
   count_launch();
   return cudaGetLastError();
@@ -1034,16 +1043,15 @@ cudaError_t launch_entropy_eig(double2* gram, int64_t walkers, int n, double* d,
 namespace {
 constexpr size_t kPanelSmemMax = 220 * 1024;  // dynamic shared memory of the panel kernel
 template <int WARPS, bool VWS>
-void panel_launch(double2* gram, const double* S, int64_t walkers, int n, int p0, int nbp,
-                  double2* P, int64_t pstride, double* d, double* e, size_t sm, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tri_panel_kernel<WARPS, VWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kPanelSmemMax);
-    attr = true;
-  }
+cudaError_t panel_launch(double2* gram, const double* S, int64_t walkers, int n, int p0, int nbp,
+                         double2* P, int64_t pstride, double* d, double* e, size_t sm,
+                         cudaStream_t st) {
+  static bool attr[kAttrDevices] = {};
+  const cudaError_t err = smem_limit(tri_panel_kernel<WARPS, VWS>, (int)kPanelSmemMax, attr);
+  if (err != cudaSuccess) return err;
   tri_panel_kernel<WARPS, VWS><<<(unsigned)walkers, WARPS * 32, sm, st>>>(gram, S, n, p0, nbp, P,
                                                                            pstride, d, e);
+  return cudaSuccess;
 }
 }  // namespace
 
@@ -1058,10 +1066,13 @@ cudaError_t launch_tri_panel(double2* gram, const double* S, int64_t walkers, in
   const size_t base = (2 + (size_t)kPanelWarps) * n * sizeof(double2);
   const size_t vw = 2 * (size_t)nbp * (n - p0) * sizeof(double2);
   if (base > kPanelSmemMax) return cudaErrorInvalidValue;
-  if (base + vw <= kPanelSmemMax)
-    panel_launch<kPanelWarps, true>(gram, S, walkers, n, p0, nbp, P, pstride, d, e, base + vw, st);
-  else
-    panel_launch<kPanelWarps, false>(gram, S, walkers, n, p0, nbp, P, pstride, d, e, base, st);
+  const cudaError_t err =
+      base + vw <= kPanelSmemMax
+          ? panel_launch<kPanelWarps, true>(gram, S, walkers, n, p0, nbp, P, pstride, d, e,
+                                            base + vw, st)
+          : panel_launch<kPanelWarps, false>(gram, S, walkers, n, p0, nbp, P, pstride, d, e, base,
+                                             st);
+  if (err != cudaSuccess) return err;
   count_launch();
   return cudaGetLastError();
 }
@@ -1105,11 +1116,9 @@ cudaError_t launch_tri_tail(double2* gram, int64_t walkers, int n, int p0, doubl
 cudaError_t launch_entropy_bisect(const double* d, const double* e, int64_t walkers, int n,
                                   double* entropy, double* eigs, cudaStream_t st) {
   if (walkers <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr = true;
-  }
+  static bool attr[kAttrDevices] = {};
+  const cudaError_t err = smem_limit(bisect_kernel, 96 * 1024, attr);
+  if (err != cudaSuccess) return err;
   const size_t sm2 = 3 * (size_t)n * sizeof(double) + (kEntThreads + 1) * sizeof(int) +
                      2 * (size_t)n * sizeof(float);
   bisect_kernel<<<(unsigned)walkers, kEntThreads, sm2, st>>>(d, e, n, entropy, eigs);

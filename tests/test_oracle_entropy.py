@@ -100,3 +100,18 @@ def test_cut_position_for_odd_spin_count():
     X = psi.reshape(M, K).T
     lam = np.linalg.eigvalsh(X @ np.conj(X.T))
     assert np.allclose(np.sort(lam)[-2:], [0.5, 0.5], atol=1e-12)
+
+
+def test_schmidt_spectrum_at_the_blocked_sizes():
+    """The closed form at the cut sizes the GPU's blocked reduction is tested
+    on (K = 256 and 512 columns of the Gram matrix), with a full and a
+    rank-deficient spectrum."""
+    rng = np.random.default_rng(61)
+    for S, split in ((17, 8), (19, 9)):
+        M, K = 1 << (S - split), 1 << split
+        for r in (K, K // 3):
+            p = rng.random(r) ** 2
+            p /= p.sum()
+            psi = from_schmidt(rng, p, M, K)
+            want = float(-np.sum(p * np.log(p)))
+            assert abs(oracle.entanglement_entropy(psi, S, split) - want) <= 1e-11 * max(1.0, want)
